@@ -17,7 +17,13 @@ CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-s
 
 
 def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` next to its source if missing or stale."""
+    """Compile ``liboracle.so`` next to its source if missing or stale.
+
+    ``OPO_ORACLE_LIB`` names a prebuilt oracle library to load instead (the
+    mutation test uses it to load deliberately broken copies)."""
+    override = os.environ.get("OPO_ORACLE_LIB")
+    if override:
+        return override
     hdr = os.path.join(HERE, "opo_oracle.h")
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC), os.path.getmtime(hdr))):
