@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the OPO split-step hot path on GB300.
+
+Workload: the 2^14-point singly resonant CW OPO (100 ps window, 3 fields,
+20 mm crystal, 100 z-steps, GVM/GVD/TOD, intracavity GDD -500 fs^2, pump at
+4x threshold), FP32 fields with FP64 phase arguments.  One step is one round
+trip (entry, 100 split-step z-steps, observables, cavity) of a batch of
+independent instances of that workload (seeds differ) sized to fill the GPU
+with one thread-block cluster per instance, run by the fused persistent
+kernel.  Metric: field-steps/s (one length-N field through one full z-step).
+
+Also reported: the same instance alone on the fused and on the plain
+(one-kernel-per-operation, graph-replayed) path; an end-to-end number
+through the C ABI with host buffers; the FP64 CPU oracle as the CPU baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun), each rank runs its own batch
+(weak scaling, no collective on the data path); timing is the max over
+ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SSFM field-steps/s at N=2^14 (fused, batched round trips)"
+UNIT = "field-steps/s"
+PEAK_SM_MHZ = 2070.0          # GB300 maximum SM clock
+SMS = 152
+FP32_LANES = 128              # FP32 FMA lanes per SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=0, help="instances per GPU (0: fill the GPU)")
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="only the headline number (no plain/e2e/cpu legs)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def flops_per_roundtrip(cfg):
+    """Algorithmic FLOPs of one round trip of one instance (the design doc's model).
+
+    per point-field per z-step: two FFTs 2 * 5 log2 N, dispersion multiply 6,
+    two RK4 half steps 2 * rk4 where rk4 = 58 (3 fields) / 62 (2 fields) per
+    point-field, +24 / +18 with the e^{i dk z} factor; per round trip and
+    point-field: cavity FFT pair 10 log2 N plus 6 (spectral factor) plus 6
+    (mirror).
+    """
+    n, F, nz = cfg.n, cfg.nfields, cfg.nz
+    lg = math.log2(n)
+    if F == 3:
+        rk4 = 58.0 + (24.0 if cfg.dk != 0 else 0.0)
+    else:
+        rk4 = 62.0 + (18.0 if cfg.dk != 0 else 0.0)
+    per_step = 10.0 * lg + 6.0 + 2.0 * rk4
+    per_rt = 10.0 * lg + 12.0
+    return n * F * (nz * per_step + per_rt)
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
+                   samples=len(rows))
+        return out
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle as it stands, one round trip of one instance per
+    step, single-threaded on the host."""
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    from oracle import oracle as orc
+    from paper_2410_02532_gb300 import workloads as W
+    cfg = W.cw_sro_16k()
+    p = orc.params(cfg)
+    pump = orc.pump_profile(p, cfg.pump_kind, cfg.pump_power, cfg.pump_fwhm)
+    a = cfg.initial_fields()
+    m = 0
+    for _ in range(args.warmup):
+        a, _, _, _ = orc.run(p, a, pump, m, 1)
+        m += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        a, _, _, _ = orc.run(p, a, pump, m, 1)
+        m += 1
+    dt = time.perf_counter() - t0
+    fs = cfg.nfields * cfg.nz * args.steps
+    val = fs / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded noise)",
+        "config": {"workload": cfg.name + " x1 instance (oracle sample)", "n": cfg.n,
+                   "fields": cfg.nfields, "nz": cfg.nz, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d round trips of one 2^14-point instance" % args.steps},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(seconds):
+    from oracle import oracle as orc
+    from paper_2410_02532_gb300 import workloads as W
+    cfg = W.cw_sro_16k()
+    p = orc.params(cfg)
+    pump = orc.pump_profile(p, cfg.pump_kind, cfg.pump_power, cfg.pump_fwhm)
+    a = cfg.initial_fields()
+    t0 = time.perf_counter()
+    rts = 0
+    while True:
+        a, _, _, _ = orc.run(p, a, pump, rts, 1)
+        rts += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": cfg.nfields * cfg.nz * rts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d round trip(s) of one 2^14-point, 3-field, 100-step instance "
+                      "(FP64, single thread, %.1f s)" % (rts, dt)}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    from paper_2410_02532_gb300 import opo
+    from paper_2410_02532_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    prec = opo.OPO_FP32_PH64 if args.precision == "fp32" else opo.OPO_FP64
+    base = W.cw_sro_16k()
+
+    def make(i, s=stream):
+        c = base.replace(instance=rank * 100000 + i)
+        return opo.Context(c, precision=prec, device=local, stream=s.cuda_stream if s else None)
+
+    probe = make(0)
+    active, cluster = opo.opo_fused_capacity(probe.h, args.cluster)
+    B = args.batch if args.batch > 0 else max(1, active)
+    ctxs = [probe] + [make(i) for i in range(1, B)]
+    batch = opo.opo_batch_create([c.h for c in ctxs], cluster)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            opo.opo_batch_run(batch, 1)
+        barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()  # evict L2 between timed steps (outside the events)
+            evs[k][0].record(stream)
+            opo.opo_batch_run(batch, 1)
+            evs[k][1].record(stream)
+        barrier()
+        clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    field_steps = base.nfields * base.nz * B * world
+    value = field_steps / (ms_per_step * 1e-3)
+    for c in ctxs:
+        c.sync()
+
+    flops_rt = flops_per_roundtrip(base)
+    achieved = flops_rt * B / (statistics.median(step_ms) * 1e-3) / 1e12
+    peak = SMS * FP32_LANES * 2 * PEAK_SM_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "note": "FP32 vector peak from 152 SMs x 128 lanes x 2 x 2070 MHz; achieved = "
+                        "algorithmic FLOPs of the batch round trip / median step time "
+                        "(the fused kernel plus one finalize launch)"}
+
+    extras = {}
+    if not args.skip_extras and rank == 0:
+        extras = single_and_plain(args, opo, W, base, prec, local, torch)
+        extras["e2e"] = e2e(args, opo, W, ctxs, batch, base, torch, np)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == opo.OPO_FP32_PH64 else "f64",
+            "data": "synthetic (seeded noise, random-phase start)",
+            "config": {"workload": "%s x %d instances per GPU (one cluster of %d CTAs each)"
+                                   % (base.name, B, cluster),
+                       "n": base.n, "fields": base.nfields, "nz": base.nz,
+                       "instances_per_gpu": B, "cluster": cluster,
+                       "precision": "fp32 fields + fp64 phase args" if prec else "fp64",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "instances sharded per GPU, no collective"},
+            "round_trips_per_s": B * world / (ms_per_step * 1e-3),
+            "roofline": roofline,
+            "clocks": clk,
+            "gpu_launches": 2 * args.steps,
+        }
+        line.update({k: v for k, v in extras.items() if k != "e2e"})
+        if "e2e" in extras:
+            line["e2e"] = extras["e2e"]
+        if world == 1 and not args.skip_extras:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    opo.opo_batch_destroy(batch)
+    for c in ctxs:
+        c.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def single_and_plain(args, opo, W, base, prec, local, torch):
+    """One instance alone: fused and plain paths, round trips per second."""
+    out = {}
+    s = torch.cuda.Stream()
+    for name, path in (("single_fused", opo.OPO_PATH_FUSED), ("single_plain", opo.OPO_PATH_PLAIN)):
+        ctx = opo.Context(base, precision=prec, device=local, stream=s.cuda_stream)
+        ctx.set_path(path)
+        steps = max(3, min(args.steps, 10))
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                opo.opo_run_roundtrips(ctx.h, 1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(steps):
+                opo.opo_run_roundtrips(ctx.h, 1)
+            e1.record(s)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_round_trip": ms, "round_trips_per_s": 1e3 / ms,
+                     "field_steps_per_s": base.nfields * base.nz * 1e3 / ms}
+        ctx.close()
+    out["fused_over_plain_single"] = (out["single_plain"]["ms_per_round_trip"]
+                                      / out["single_fused"]["ms_per_round_trip"])
+    return out
+
+
+def e2e(args, opo, W, ctxs, batch, base, torch, np):
+    """Through the C ABI with host buffers: every step copies each instance's
+    fields from pinned host memory, runs one round trip and reads the output
+    signal field and the trace row back to the host."""
+    n, F = base.n, base.nfields
+    B = len(ctxs)
+    host_in = [torch.empty((F, n, 2), dtype=torch.float64).pin_memory() for _ in range(B)]
+    host_out = torch.empty((n, 2), dtype=torch.float64).pin_memory()
+    host_tr = torch.empty((1, 4), dtype=torch.float64).pin_memory()
+    for i, c in enumerate(ctxs):
+        host_in[i].copy_(torch.from_numpy(np.stack([c.get_fields()[x].view(np.float64).reshape(n, 2)
+                                                     for x in range(F)])))
+    L = opo.lib()
+    dp = lambda t: opo.ctypes.cast(t.data_ptr(), opo._DP)  # noqa: E731
+    steps = max(3, min(args.steps, 10))
+
+    def one_step():
+        for i, c in enumerate(ctxs):
+            for x in range(F):
+                st = L.opo_set_fields(c.h, x, dp(host_in[i][x]), n, -1)
+                assert st == 0
+        opo.opo_batch_run(batch, 1)
+        for c in ctxs:
+            assert L.opo_get_fields(c.h, 1, opo.OPO_OUTPUT, dp(host_out), n) == 0
+            assert L.opo_get_trace(c.h, dp(host_tr), 1) == 0
+
+    one_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one_step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": F * base.nz * B / dt, "unit": UNIT,
+            "h2d_bytes_per_step": B * F * n * 16,
+            "d2h_bytes_per_step": B * (n * 16 + 32),
+            "ms_per_step": dt * 1e3}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

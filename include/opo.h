@@ -1,0 +1,230 @@
+/*
+ * opo.h -- C ABI of libopo.so, a GB300 (sm_103a) implementation of the hot
+ * path of an optical parametric oscillator (OPO) simulator after
+ * arXiv 2410.02532 ("cuOPO").
+ *
+ * What one round trip computes (the paper's method):
+ *   entry ........ the intracavity pump is replaced by the input pump unless
+ *                  it is resonant (Sec. 4.1, pump read-in kernel); a
+ *                  non-resonant signal/idler restarts from zero (Sec. 2.1,
+ *                  boundary conditions apply to resonant fields only)
+ *   crystal pass . nz fixed steps of the symmetrized split-step Fourier
+ *                  method N/2 - L - N/2 (Sec. 2.2, Eq. (expon)) on the
+ *                  coupled-wave equations (Sec. 2.1, Eqs. (CEp)-(CEi));
+ *                  linear operator of Eq. (linearop) in the frequency domain,
+ *                  nonlinear part by one RK4 step of dz/2 per half step
+ *   observables .. output-coupled power per field and the signal spectral
+ *                  centroid of this round trip
+ *   cavity ....... on resonant fields: intracavity GDD and timing mismatch in
+ *                  the frequency domain (Sec. 2.3 item 1), then the mirror
+ *                  sqrt(1 - theta) e^{i delta} (Sec. 2.1, Eq. (BC)), then the
+ *                  phase modulator (Sec. 2.3 item 2), in the order of the
+ *                  main-loop listing of Sec. 4.1
+ *
+ * Conventions (where the paper is silent; every one is fixed by a test):
+ *   - grid: N points over the window T = t_rt, dt = T/N, dnu = 1/T
+ *     (Sec. 2.4); tau_n = (n - N/2) dt; Omega_k = 2 pi k'/T with k' = k for
+ *     k < N/2 and k - N otherwise;
+ *   - DFT X_k = sum_n A_n e^{-2 pi i k n/N}, so d/dtau <-> +i Omega;
+ *   - linear step factor per dz:
+ *       D_x = exp{dz [-alpha_x/2 + i(-dbeta1_x Omega + beta2_x Omega^2/2
+ *                                    - beta3_x Omega^3/tod_div)]},
+ *     with dbeta1_x = 1/nu_x - 1/nu_s (a slower field moves to later tau) and
+ *     tod_div = 6 (Taylor; the paper prints 3, reachable through tod_div);
+ *   - two-field (degenerate) mode: dA_p/dz = i (kappa_p/2) A_s^2 e^{-i dk z},
+ *     dA_s/dz = i kappa_s A_p A_s* e^{+i dk z};
+ *   - kappa_x = 2 pi d_eff / (n_x lambda_x); power P = mean|A|^2 n eps0 c/2
+ *     times pi w0^2;
+ *   - EOM phase beta sin(2 pi frac(f_pm (tau_n + m t_rt))) at round trip m;
+ *   - timing mismatch: resonant spectra times e^{-i Omega delay_s} per round
+ *     trip (a positive delay moves the field to later tau).
+ *
+ * Field index: 0 = pump, 1 = signal, 2 = idler (two-field mode: 0, 1).
+ * Units are SI.  Host arrays of complex values are interleaved (re, im)
+ * doubles; the caller owns every host buffer, the library copies inputs and
+ * writes outputs into caller buffers and owns all device memory of a context.
+ *
+ * Errors: every entry point returns an opo_status and never aborts or exits.
+ * Work is enqueued on the context's stream; device-side errors (non-finite
+ * fields) surface as OPO_E_NONFINITE at the next synchronizing call
+ * (opo_run_roundtrips with stats, opo_get_fields, opo_get_trace, opo_sync).
+ * A context is not thread-safe; distinct contexts may be used from distinct
+ * threads.
+ */
+#ifndef OPO_H
+#define OPO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OPO_API __attribute__((visibility("default")))
+#else
+#define OPO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct opo_ctx opo_ctx;     /* opaque, library-owned */
+typedef struct opo_batch opo_batch; /* opaque, library-owned */
+
+typedef enum {
+    OPO_OK = 0,
+    OPO_E_INVALID = 1,     /* bad argument (null pointer, size, range, non-finite value) */
+    OPO_E_NOMEM = 2,       /* device allocation failed */
+    OPO_E_CUDA = 3,        /* a CUDA runtime call failed (no device, launch failure ...) */
+    OPO_E_NONFINITE = 4,   /* a field became NaN/Inf (dz too large, Sec. 2.4) */
+    OPO_E_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    OPO_E_STATE = 6,       /* call out of order (crystal or cavity not set) */
+    OPO_E_UNSUPPORTED = 7  /* valid request the chosen path cannot run */
+} opo_status;
+
+enum { OPO_FP64 = 0, OPO_FP32_PH64 = 1 };               /* opo_grid.precision */
+enum { OPO_PUMP_CW = 0, OPO_PUMP_SECH2 = 1, OPO_PUMP_USER = 2 };
+enum { OPO_INTRACAVITY = 0, OPO_OUTPUT = 1 };           /* opo_get_fields which */
+enum { OPO_PATH_AUTO = 0, OPO_PATH_PLAIN = 1, OPO_PATH_FUSED = 2 };
+
+/* Grid and numerics of one OPO instance (Sec. 2.4). */
+typedef struct {
+    int32_t n;           /* points N: power of two in [16, 131072]                 */
+    double  t_window_s;  /* window T = t_rt [s], > 0                               */
+    int32_t nfields;     /* 3 (pump, signal, idler) or 2 (degenerate)              */
+    int32_t precision;   /* OPO_FP64: all FP64.  OPO_FP32_PH64: FP32 complex
+                            fields, phase arguments formed in FP64 and rounded
+                            once                                                    */
+    int32_t device;      /* CUDA device ordinal                                     */
+    void   *stream;      /* cudaStream_t to enqueue on; NULL: the context makes a
+                            private non-blocking stream                            */
+} opo_grid;
+
+/* Nonlinear crystal (Sec. 2.1).  Triples are indexed by field. */
+typedef struct {
+    double  length_m;           /* L > 0                                           */
+    int32_t nz;                 /* fixed z-steps per pass, >= 1                    */
+    double  dk_per_m;           /* Delta k = k_p - k_s - k_i                       */
+    double  deff_mpv;           /* d_eff [m/V]                                     */
+    double  lambda_m[3];        /* vacuum wavelengths, > 0 for used fields         */
+    double  n[3];               /* refractive indices, > 0 for used fields         */
+    double  alpha_per_m[3];     /* power attenuation                               */
+    double  dbeta1_s_per_m[3];  /* 1/nu_x - 1/nu_s                                 */
+    double  beta2_s2_per_m[3];  /* GVD k''                                         */
+    double  beta3_s3_per_m[3];  /* TOD k'''                                        */
+    double  w0_m;               /* beam waist for power <-> intensity, > 0         */
+    double  tod_div;            /* divisor of the TOD term; 0 selects 6            */
+} opo_crystal;
+
+/* Cavity and pump (Sec. 2.1 Eq. (BC), Sec. 2.3, Sec. 4). */
+typedef struct {
+    uint32_t resonant_mask;  /* bit x: field x resonant (SRO/DRO/TRO, Sec. 4.2)    */
+    double  R[3];            /* mirror power reflectivity 1 - theta_x, in [0, 1]   */
+    double  delta_rad[3];    /* detuning phase delta_x (Eq. (BC))                  */
+    double  gdd_s2[3];       /* intracavity GDD gamma_x [s^2] (Sec. 2.3 item 1)    */
+    double  delay_s;         /* per-round-trip timing mismatch of resonant fields  */
+    double  eom_beta_rad;    /* EOM depth beta (Sec. 2.3 item 2); 0 = no EOM       */
+    double  eom_f_hz;        /* EOM frequency f_pm                                 */
+    double  t_rt_s;          /* round-trip time in the EOM phase; 0 = t_window_s   */
+    int32_t pump_kind;       /* OPO_PUMP_CW / _SECH2 / _USER                        */
+    double  pump_power_W;    /* CW power, or sech^2 peak power                     */
+    double  pump_fwhm_s;     /* sech^2 intensity FWHM                              */
+    const double *pump_user; /* OPO_PUMP_USER: 2N interleaved doubles [V/m], copied */
+} opo_cavity;
+
+/* Result of opo_run_roundtrips (filled only when a pointer is passed, which
+ * synchronizes the stream). */
+typedef struct {
+    int64_t rt_done;          /* round-trip counter m after the call               */
+    double  p_out_W[3];       /* output-coupled power per field, last round trip   */
+    double  centroid_hz;      /* signal spectral centroid, last round trip         */
+    double  p_out_mean_W[3];  /* mean over the last max(10, ceil(M/10)) round trips */
+    double  centroid_mean_hz; /* of this call (all of them if M < 10)              */
+    int32_t path;             /* OPO_PATH_PLAIN or OPO_PATH_FUSED                  */
+    int32_t cluster;          /* CTAs per instance of the fused path (0: plain)    */
+} opo_stats;
+
+/* Create a context for one OPO instance on grid->device.  Fields start at
+ * zero; a zero signal never grows, so seed it with opo_set_fields.
+ * Returns OPO_E_INVALID for a bad grid, OPO_E_CUDA if the device is missing,
+ * OPO_E_NOMEM if allocation fails.  *out is NULL on failure. */
+OPO_API int opo_create(opo_ctx **out, const opo_grid *grid);
+
+/* Set the crystal (Sec. 2.1); rebuilds the per-step dispersion factors D_x
+ * (FP64 arguments, one rounding) on the device.  Copies *crystal. */
+OPO_API int opo_set_crystal(opo_ctx *ctx, const opo_crystal *crystal);
+
+/* Set the cavity and pump (Eq. (BC), Sec. 2.3); rebuilds the input pump, GDD
+ * and delay factors on the device.  Copies *cavity and pump_user. */
+OPO_API int opo_set_cavity(opo_ctx *ctx, const opo_cavity *cavity);
+
+/* Copy n complex values (2n interleaved doubles) into intracavity field
+ * `field`; n must equal the grid's N.  rt_index >= 0 also sets the
+ * round-trip counter m (the EOM phase depends on it); -1 leaves it. */
+OPO_API int opo_set_fields(opo_ctx *ctx, int32_t field, const double *interleaved, size_t n,
+                   int64_t rt_index);
+
+/* Run m >= 0 round trips, enqueued on the context's stream.  stats may be
+ * NULL (no synchronization); otherwise the call waits and fills it.
+ * OPO_E_STATE before both opo_set_crystal and opo_set_cavity. */
+OPO_API int opo_run_roundtrips(opo_ctx *ctx, int64_t m, opo_stats *stats);
+
+/* Copy field `field` into out (2n doubles, n = N).  which = OPO_INTRACAVITY:
+ * the state that starts the next round trip; OPO_OUTPUT: the output-coupled
+ * field sqrt(1 - R_x) A_x (resonant) or A_x (non-resonant) of the last round
+ * trip, zero before the first.  Synchronizes the stream. */
+OPO_API int opo_get_fields(opo_ctx *ctx, int32_t field, int32_t which, double *out, size_t n);
+
+/* Copy the per-round-trip observables of the last opo_run_roundtrips call:
+ * rows {P_p_out, P_s_out, P_i_out, nu_c} [W, W, W, Hz], `rows` rows (at most
+ * the call's M).  Synchronizes. */
+OPO_API int opo_get_trace(opo_ctx *ctx, double *out, int64_t rows);
+
+/* Device-resident variants for callers that keep fields on the GPU (for
+ * example in torch tensors): dev points to n complex values in the
+ * context's precision (float2 or double2 interleaved) on the context's
+ * device.  Stream-ordered; no synchronization. */
+OPO_API int opo_set_fields_device(opo_ctx *ctx, int32_t field, const void *dev, size_t n,
+                          int64_t rt_index);
+OPO_API int opo_get_fields_device(opo_ctx *ctx, int32_t field, int32_t which, void *dev, size_t n);
+
+/* Choose the execution path.  OPO_PATH_PLAIN: one kernel per operation per
+ * z-step, replayed as a CUDA graph per round trip.  OPO_PATH_FUSED: one
+ * persistent kernel per launch in which a thread-block cluster of `cluster`
+ * CTAs keeps the instance's fields in distributed shared memory for
+ * `rt_per_launch` round trips.  cluster = 0 / rt_per_launch = 0 pick
+ * defaults.  OPO_E_UNSUPPORTED if the fused path cannot hold this instance. */
+OPO_API int opo_set_path(opo_ctx *ctx, int32_t path, int32_t cluster, int32_t rt_per_launch);
+
+/* Fused-path capacity on the context's device: how many thread-block
+ * clusters of `cluster` CTAs (0: the default size for this instance) with
+ * this instance's shared-memory footprint can be resident at once, i.e. how
+ * many such instances one batched launch runs concurrently.  *cluster_out
+ * (optional) receives the cluster size used.  OPO_E_UNSUPPORTED if the fused
+ * path cannot hold the instance. */
+OPO_API int opo_fused_capacity(const opo_ctx *ctx, int32_t cluster, int32_t *max_active,
+                               int32_t *cluster_out);
+
+/* Wait for the context's stream; reports a pending device error. */
+OPO_API int opo_sync(opo_ctx *ctx);
+
+/* Free the context and its device memory (NULL is accepted). */
+OPO_API int opo_destroy(opo_ctx *ctx);
+
+/* Static string for a status code. */
+OPO_API const char *opo_status_string(int status);
+
+/* Batched sweep: many instances in one fused launch, one thread-block cluster
+ * per instance.  All contexts must be on one device, in one precision, with
+ * crystal and cavity set; N, field count, nz and every parameter may differ.
+ * The batch keeps pointers to the contexts (which stay owned by the caller
+ * and must outlive the batch) and runs on the first context's stream.
+ * Each instance advances exactly as opo_run_roundtrips would advance it on
+ * the fused path with the same cluster size. */
+OPO_API int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster);
+OPO_API int opo_batch_run(opo_batch *batch, int64_t m);
+OPO_API int opo_batch_destroy(opo_batch *batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OPO_H */

@@ -1,0 +1,728 @@
+// opo_abi.cu -- the C ABI of libopo.so (declared in include/opo.h): context
+// lifecycle, argument validation, device memory, path selection (plain
+// per-operation graph or fused persistent cluster kernel), the batched
+// sweep, field transfer and the per-round-trip trace.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "opo_common.cuh"
+#include "opo_internal.h"
+
+using namespace opo;
+
+namespace {
+
+// Make the context's device current for the duration of a call and restore
+// the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return OPO_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return OPO_E_NOMEM;
+    return OPO_E_CUDA;
+}
+
+bool finite_all(const double *v, int k)
+{
+    for (int i = 0; i < k; i++)
+        if (!std::isfinite(v[i]))
+            return false;
+    return true;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+template <class T>
+__global__ void k_from_f64(cv<T> *dst, const double *src, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = cmk<cv<T>>((T)src[2 * i], (T)src[2 * i + 1]);
+}
+
+template <class T>
+__global__ void k_to_f64(double *dst, const cv<T> *src, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        cv<T> v = src[i];
+        dst[2 * i] = (double)v.x;
+        dst[2 * i + 1] = (double)v.y;
+    }
+}
+
+__global__ void k_ctl_begin(DevCtl *ctl, int64_t rt0, double *obs, int parts)
+{
+    ctl->rt0 = rt0;
+    ctl->slot = 0;
+    ctl->obs = obs;
+    ctl->parts = parts;
+}
+
+int blocks(int64_t work)
+{
+    int64_t b = (work + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 4096));
+}
+
+void free_all(opo_ctx *c)
+{
+    void *bufs[] = {c->d_fields, c->d_out, c->d_scratch, c->d_pump, c->d_disp, c->d_gdd,
+                    c->d_tw, c->d_ekz, c->d_pump_user, c->d_obs, c->d_trace, c->d_ctl,
+                    c->d_stage};
+    for (void *b : bufs)
+        if (b)
+            cudaFree(b);
+    if (c->h_pinned)
+        cudaFreeHost(c->h_pinned);
+    if (c->graph)
+        cudaGraphExecDestroy(c->graph);
+    if (c->capture_stream)
+        cudaStreamDestroy(c->capture_stream);
+    if (c->own_stream && c->stream)
+        cudaStreamDestroy(c->stream);
+}
+
+int derive(opo_ctx *c)
+{
+    const opo_crystal &k = c->crystal;
+    const opo_cavity &v = c->cavity;
+    Derived &d = c->dv;
+    for (int x = 0; x < 3; x++) {
+        d.kappa[x] = (x < c->F) ? 2.0 * kPi * k.deff_mpv / (k.n[x] * k.lambda_m[x]) : 0.0;
+        d.pscale[x] = (x < c->F) ? 0.5 * k.n[x] * kEps0 * kC0 * kPi * k.w0_m * k.w0_m : 0.0;
+        bool res = (v.resonant_mask >> x) & 1u;
+        double r = res ? std::sqrt(v.R[x]) : 1.0;
+        d.bc_re[x] = res ? r * std::cos(v.delta_rad[x]) : 1.0;
+        d.bc_im[x] = res ? r * std::sin(v.delta_rad[x]) : 0.0;
+        d.outscale[x] = res ? std::sqrt(1.0 - v.R[x]) : 1.0;
+    }
+    d.dz = k.length_m / (double)k.nz;
+    d.h = 0.5 * d.dz;
+    d.use_dk = k.dk_per_m != 0.0;
+    d.eom = v.eom_beta_rad != 0.0;
+    return OPO_OK;
+}
+
+int ensure_obs(opo_ctx *c, int64_t M, int parts)
+{
+    int64_t need = std::max<int64_t>(M, 1);
+    if (need <= c->obs_cap && parts <= c->obs_parts_cap)
+        return OPO_OK;
+    int64_t cap = std::max<int64_t>(need, 2 * c->obs_cap);
+    int pc = std::max(parts, c->obs_parts_cap);
+    double *o = nullptr, *t = nullptr;
+    cudaStreamSynchronize(c->stream);
+    if (cudaMalloc((void **)&o, sizeof(double) * cap * pc * kNslot) != cudaSuccess)
+        return OPO_E_NOMEM;
+    if (cudaMalloc((void **)&t, sizeof(double) * cap * 4) != cudaSuccess) {
+        cudaFree(o);
+        return OPO_E_NOMEM;
+    }
+    // keep the previous call's trace readable
+    if (c->d_trace)
+        cudaMemcpy(t, c->d_trace, sizeof(double) * std::min(c->obs_cap, cap) * 4,
+                   cudaMemcpyDeviceToDevice);
+    if (c->d_obs)
+        cudaFree(c->d_obs);
+    if (c->d_trace)
+        cudaFree(c->d_trace);
+    c->d_obs = o;
+    c->d_trace = t;
+    c->obs_cap = cap;
+    c->obs_parts_cap = pc;
+    return OPO_OK;
+}
+
+int check_err(opo_ctx *c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return OPO_E_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, (char *)c->d_ctl + offsetof(DevCtl, err), sizeof(int),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return OPO_E_CUDA;
+    return err ? OPO_E_NONFINITE : OPO_OK;
+}
+
+int build_graph(opo_ctx *c)
+{
+    if (c->graph_valid)
+        return OPO_OK;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    plain_prepare(c);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return OPO_E_CUDA;
+    int rc = plain_enqueue_roundtrip(c, c->capture_stream);
+    cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
+    if (rc != OPO_OK || e != cudaSuccess) {
+        if (g)
+            cudaGraphDestroy(g);
+        cudaGetLastError();
+        return OPO_E_CUDA;
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+        return OPO_E_CUDA;
+    c->graph_valid = true;
+    return OPO_OK;
+}
+
+// Validate the ranges shared by crystal and cavity checks.
+bool valid_crystal(const opo_ctx *c, const opo_crystal *k)
+{
+    if (!(k->length_m > 0.0) || !std::isfinite(k->length_m) || k->nz < 1 || k->nz > 1000000)
+        return false;
+    if (!std::isfinite(k->dk_per_m) || !std::isfinite(k->deff_mpv) || !(k->w0_m > 0.0) ||
+        !std::isfinite(k->w0_m) || !std::isfinite(k->tod_div) || k->tod_div < 0.0)
+        return false;
+    if (!finite_all(k->lambda_m, 3) || !finite_all(k->n, 3) || !finite_all(k->alpha_per_m, 3) ||
+        !finite_all(k->dbeta1_s_per_m, 3) || !finite_all(k->beta2_s2_per_m, 3) ||
+        !finite_all(k->beta3_s3_per_m, 3))
+        return false;
+    for (int x = 0; x < c->F; x++)
+        if (!(k->lambda_m[x] > 0.0) || !(k->n[x] > 0.0))
+            return false;
+    return true;
+}
+
+bool valid_cavity(const opo_ctx *c, const opo_cavity *v)
+{
+    if (v->resonant_mask >> c->F)
+        return false;
+    for (int x = 0; x < 3; x++)
+        if (!(v->R[x] >= 0.0 && v->R[x] <= 1.0))
+            return false;
+    if (!finite_all(v->delta_rad, 3) || !finite_all(v->gdd_s2, 3) || !std::isfinite(v->delay_s) ||
+        !std::isfinite(v->eom_beta_rad) || !std::isfinite(v->eom_f_hz) ||
+        !std::isfinite(v->t_rt_s) || v->t_rt_s < 0.0 || !std::isfinite(v->pump_power_W) ||
+        v->pump_power_W < 0.0 || !std::isfinite(v->pump_fwhm_s))
+        return false;
+    if (v->pump_kind < OPO_PUMP_CW || v->pump_kind > OPO_PUMP_USER)
+        return false;
+    if (v->pump_kind == OPO_PUMP_SECH2 && !(v->pump_fwhm_s > 0.0))
+        return false;
+    if (v->pump_kind == OPO_PUMP_USER) {
+        if (!v->pump_user)
+            return false;
+        if (!finite_all(v->pump_user, 2 * c->n))
+            return false;
+    }
+    return true;
+}
+
+int choose_path(opo_ctx *c, FusedCfg *cfg)
+{
+    if (c->path_req == OPO_PATH_PLAIN)
+        return OPO_PATH_PLAIN;
+    bool ok = fused_config(c->csz, c->F, c->n, c->n, c->cluster_req, c->rtpl_req, cfg);
+    if (c->path_req == OPO_PATH_FUSED)
+        return ok ? OPO_PATH_FUSED : -1;
+    return ok ? OPO_PATH_FUSED : OPO_PATH_PLAIN;
+}
+
+// Observable storage for M round trips; the plain path also resets the
+// device control block its captured graph reads.
+int begin_call(opo_ctx *c, int64_t M, int parts, bool plain)
+{
+    int rc = ensure_obs(c, M, parts);
+    if (rc != OPO_OK || !plain)
+        return rc;
+    k_ctl_begin<<<1, 1, 0, c->stream>>>(c->d_ctl, c->rt, c->d_obs, parts);
+    return cuda_status(cudaGetLastError());
+}
+
+} // namespace
+
+extern "C" {
+
+const char *opo_status_string(int s)
+{
+    switch (s) {
+    case OPO_OK: return "ok";
+    case OPO_E_INVALID: return "invalid argument";
+    case OPO_E_NOMEM: return "device allocation failed";
+    case OPO_E_CUDA: return "CUDA runtime error";
+    case OPO_E_NONFINITE: return "non-finite field (step dz too large?)";
+    case OPO_E_TIMEOUT: return "device wait timed out";
+    case OPO_E_STATE: return "call out of order (crystal or cavity not set)";
+    case OPO_E_UNSUPPORTED: return "unsupported by the requested path";
+    default: return "unknown status";
+    }
+}
+
+int opo_create(opo_ctx **out, const opo_grid *grid)
+{
+    if (!out)
+        return OPO_E_INVALID;
+    *out = nullptr;
+    if (!grid)
+        return OPO_E_INVALID;
+    if (!is_pow2(grid->n) || grid->n < 16 || grid->n > (1 << 17))
+        return OPO_E_INVALID;
+    if (!(grid->t_window_s > 0.0) || !std::isfinite(grid->t_window_s))
+        return OPO_E_INVALID;
+    if (grid->nfields != 2 && grid->nfields != 3)
+        return OPO_E_INVALID;
+    if (grid->precision != OPO_FP64 && grid->precision != OPO_FP32_PH64)
+        return OPO_E_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return OPO_E_CUDA;
+    }
+    if (grid->device < 0 || grid->device >= ndev)
+        return OPO_E_INVALID;
+    DeviceGuard g(grid->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    opo_ctx *c = new (std::nothrow) opo_ctx();
+    if (!c)
+        return OPO_E_NOMEM;
+    c->grid = *grid;
+    c->device = grid->device;
+    c->n = grid->n;
+    c->logn = ilog2((unsigned)grid->n);
+    c->F = grid->nfields;
+    c->prec = grid->precision;
+    c->csz = c->prec == OPO_FP64 ? sizeof(double2) : sizeof(float2);
+    int rc = OPO_OK;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (rc != OPO_OK)
+            return;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess)
+            rc = cuda_status(e);
+    };
+    const size_t fb = c->csz * (size_t)c->F * c->n;
+    alloc(&c->d_fields, fb);
+    alloc(&c->d_out, fb);
+    alloc(&c->d_scratch, fb);
+    alloc(&c->d_disp, fb);
+    alloc(&c->d_gdd, fb);
+    alloc(&c->d_pump, c->csz * c->n);
+    alloc(&c->d_tw, c->csz * c->n);
+    alloc((void **)&c->d_pump_user, sizeof(double) * 2 * c->n);
+    alloc((void **)&c->d_stage, sizeof(double) * 2 * c->n);
+    alloc((void **)&c->d_ctl, sizeof(DevCtl));
+    if (rc == OPO_OK) {
+        if (grid->stream) {
+            c->stream = (cudaStream_t)grid->stream;
+        } else {
+            rc = cuda_status(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+            c->own_stream = rc == OPO_OK;
+        }
+    }
+    if (rc == OPO_OK)
+        rc = cuda_status(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    if (rc == OPO_OK) {
+        cudaMemsetAsync(c->d_fields, 0, fb, c->stream);
+        cudaMemsetAsync(c->d_out, 0, fb, c->stream);
+        cudaMemsetAsync(c->d_ctl, 0, sizeof(DevCtl), c->stream);
+        rc = setup_twiddles(c);
+    }
+    if (rc == OPO_OK)
+        rc = cuda_status(cudaStreamSynchronize(c->stream));
+    if (rc != OPO_OK) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return OPO_OK;
+}
+
+int opo_destroy(opo_ctx *c)
+{
+    if (!c)
+        return OPO_OK;
+    DeviceGuard g(c->device);
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return OPO_OK;
+}
+
+int opo_set_crystal(opo_ctx *c, const opo_crystal *k)
+{
+    if (!c || !k)
+        return OPO_E_INVALID;
+    if (!valid_crystal(c, k))
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    c->crystal = *k;
+    int cnt = 4 * k->nz + 1;
+    if (cnt > c->ekz_cap) {
+        cudaStreamSynchronize(c->stream);
+        if (c->d_ekz)
+            cudaFree(c->d_ekz);
+        c->d_ekz = nullptr;
+        c->ekz_cap = 0;
+        if (cudaMalloc(&c->d_ekz, c->csz * cnt) != cudaSuccess)
+            return OPO_E_NOMEM;
+        c->ekz_cap = cnt;
+    }
+    c->have_crystal = true;
+    c->graph_valid = false;
+    derive(c);
+    int rc = setup_crystal_tables(c);
+    if (rc == OPO_OK && c->have_cavity)
+        rc = setup_cavity_tables(c); // pump amplitude depends on n_p and w0
+    return rc;
+}
+
+int opo_set_cavity(opo_ctx *c, const opo_cavity *v)
+{
+    if (!c || !v)
+        return OPO_E_INVALID;
+    if (!valid_cavity(c, v))
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    c->cavity = *v;
+    c->cavity.pump_user = nullptr;
+    if (v->pump_kind == OPO_PUMP_USER) {
+        if (cudaMemcpyAsync(c->d_pump_user, v->pump_user, sizeof(double) * 2 * c->n,
+                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return OPO_E_CUDA;
+    }
+    c->have_cavity = true;
+    c->graph_valid = false;
+    if (c->have_crystal) {
+        derive(c);
+        return setup_cavity_tables(c);
+    }
+    return OPO_OK;
+}
+
+static int set_fields_impl(opo_ctx *c, int32_t field, const void *src, size_t n, int64_t rt_index,
+                           bool device_src)
+{
+    if (!c || !src || field < 0 || field >= c->F || n != (size_t)c->n)
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    char *dst = (char *)c->d_fields + (size_t)field * c->n * c->csz;
+    cudaError_t e;
+    if (device_src) {
+        e = cudaMemcpyAsync(dst, src, c->csz * n, cudaMemcpyDeviceToDevice, c->stream);
+    } else {
+        e = cudaMemcpyAsync(c->d_stage, src, sizeof(double) * 2 * n, cudaMemcpyHostToDevice,
+                            c->stream);
+        if (e == cudaSuccess) {
+            if (c->prec == OPO_FP64)
+                k_from_f64<double><<<blocks(c->n), 256, 0, c->stream>>>((double2 *)dst, c->d_stage, c->n);
+            else
+                k_from_f64<float><<<blocks(c->n), 256, 0, c->stream>>>((float2 *)dst, c->d_stage, c->n);
+            e = cudaGetLastError();
+        }
+        // the host buffer must be free to reuse when we return
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+    }
+    if (e != cudaSuccess)
+        return OPO_E_CUDA;
+    if (rt_index >= 0)
+        c->rt = rt_index;
+    return OPO_OK;
+}
+
+int opo_set_fields(opo_ctx *c, int32_t field, const double *interleaved, size_t n, int64_t rt_index)
+{
+    return set_fields_impl(c, field, interleaved, n, rt_index, false);
+}
+
+int opo_set_fields_device(opo_ctx *c, int32_t field, const void *dev, size_t n, int64_t rt_index)
+{
+    return set_fields_impl(c, field, dev, n, rt_index, true);
+}
+
+static int get_fields_impl(opo_ctx *c, int32_t field, int32_t which, void *dst, size_t n,
+                           bool device_dst)
+{
+    if (!c || !dst || field < 0 || field >= c->F || n != (size_t)c->n)
+        return OPO_E_INVALID;
+    if (which != OPO_INTRACAVITY && which != OPO_OUTPUT)
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    const char *src = (const char *)(which == OPO_OUTPUT ? c->d_out : c->d_fields) +
+                      (size_t)field * c->n * c->csz;
+    if (device_dst) {
+        if (cudaMemcpyAsync(dst, src, c->csz * n, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            return OPO_E_CUDA;
+        return OPO_OK;
+    }
+    if (c->prec == OPO_FP64)
+        k_to_f64<double><<<blocks(c->n), 256, 0, c->stream>>>(c->d_stage, (const double2 *)src, c->n);
+    else
+        k_to_f64<float><<<blocks(c->n), 256, 0, c->stream>>>(c->d_stage, (const float2 *)src, c->n);
+    if (cudaGetLastError() != cudaSuccess)
+        return OPO_E_CUDA;
+    if (cudaMemcpyAsync(dst, c->d_stage, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+        return OPO_E_CUDA;
+    return check_err(c);
+}
+
+int opo_get_fields(opo_ctx *c, int32_t field, int32_t which, double *out, size_t n)
+{
+    return get_fields_impl(c, field, which, out, n, false);
+}
+
+int opo_get_fields_device(opo_ctx *c, int32_t field, int32_t which, void *dev, size_t n)
+{
+    return get_fields_impl(c, field, which, dev, n, true);
+}
+
+int opo_set_path(opo_ctx *c, int32_t path, int32_t cluster, int32_t rt_per_launch)
+{
+    if (!c || path < OPO_PATH_AUTO || path > OPO_PATH_FUSED)
+        return OPO_E_INVALID;
+    if (cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)) || rt_per_launch < 0)
+        return OPO_E_INVALID;
+    if (path == OPO_PATH_FUSED) {
+        FusedCfg cfg;
+        if (!fused_config(c->csz, c->F, c->n, c->n, cluster, rt_per_launch, &cfg))
+            return OPO_E_UNSUPPORTED;
+    }
+    c->path_req = path;
+    c->cluster_req = cluster;
+    c->rtpl_req = rt_per_launch;
+    return OPO_OK;
+}
+
+int opo_run_roundtrips(opo_ctx *c, int64_t m, opo_stats *stats)
+{
+    if (!c || m < 0)
+        return OPO_E_INVALID;
+    if (!c->have_crystal || !c->have_cavity)
+        return OPO_E_STATE;
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    FusedCfg cfg{};
+    int path = choose_path(c, &cfg);
+    if (path < 0)
+        return OPO_E_UNSUPPORTED;
+    int parts = path == OPO_PATH_FUSED ? cfg.cluster : 1;
+    int rc = begin_call(c, m, parts, path == OPO_PATH_PLAIN);
+    if (rc != OPO_OK)
+        return rc;
+    if (path == OPO_PATH_PLAIN) {
+        rc = build_graph(c);
+        for (int64_t i = 0; i < m && rc == OPO_OK; i++)
+            rc = cuda_status(cudaGraphLaunch(c->graph, c->stream));
+        if (rc == OPO_OK)
+            rc = finalize_trace(c, m, parts);
+    } else if (m > 0) {
+        opo_ctx *one[1] = {c};
+        rc = fused_run(one, 1, cfg, m, c->stream);
+    }
+    if (rc != OPO_OK)
+        return rc;
+    c->rt += m;
+    c->last_M = m;
+    c->last_parts = parts;
+    c->last_path = path;
+    c->last_cluster = path == OPO_PATH_FUSED ? cfg.cluster : 0;
+    if (!stats)
+        return OPO_OK;
+    std::memset(stats, 0, sizeof(*stats));
+    stats->rt_done = c->rt;
+    stats->path = path;
+    stats->cluster = c->last_cluster;
+    rc = check_err(c);
+    if (m > 0) {
+        std::vector<double> tr((size_t)m * 4);
+        if (cudaMemcpy(tr.data(), c->d_trace, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return OPO_E_CUDA;
+        int64_t K = std::max<int64_t>(10, (m + 9) / 10);
+        K = std::min(K, m);
+        for (int x = 0; x < 3; x++) {
+            stats->p_out_W[x] = tr[(size_t)(m - 1) * 4 + x];
+            double s = 0.0;
+            for (int64_t r = m - K; r < m; r++)
+                s += tr[(size_t)r * 4 + x];
+            stats->p_out_mean_W[x] = s / (double)K;
+        }
+        stats->centroid_hz = tr[(size_t)(m - 1) * 4 + 3];
+        double s = 0.0;
+        for (int64_t r = m - K; r < m; r++)
+            s += tr[(size_t)r * 4 + 3];
+        stats->centroid_mean_hz = s / (double)K;
+    }
+    return rc;
+}
+
+int opo_get_trace(opo_ctx *c, double *out, int64_t rows)
+{
+    if (!c || !out || rows < 0 || rows > c->last_M)
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    int rc = check_err(c);
+    if (rows > 0 &&
+        cudaMemcpy(out, c->d_trace, sizeof(double) * 4 * rows, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return OPO_E_CUDA;
+    return rc;
+}
+
+int opo_fused_capacity(const opo_ctx *c, int32_t cluster, int32_t *max_active,
+                       int32_t *cluster_out)
+{
+    if (!c || !max_active || cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)))
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    FusedCfg cfg;
+    if (!fused_config(c->csz, c->F, c->n, c->n, cluster, 0, &cfg))
+        return OPO_E_UNSUPPORTED;
+    *max_active = fused_max_active(c->prec == OPO_FP64, cfg.cluster, cfg.smem);
+    if (cluster_out)
+        *cluster_out = cfg.cluster;
+    return OPO_OK;
+}
+
+int opo_sync(opo_ctx *c)
+{
+    if (!c)
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    return check_err(c);
+}
+
+} // extern "C"
+
+struct opo_batch {
+    std::vector<opo_ctx *> ctxs;
+    FusedCfg cfg;
+    std::vector<cudaEvent_t> ev;
+};
+
+extern "C" {
+
+int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster)
+{
+    if (!out)
+        return OPO_E_INVALID;
+    *out = nullptr;
+    if (!ctxs || count < 1)
+        return OPO_E_INVALID;
+    if (cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)))
+        return OPO_E_INVALID;
+    int fmax = 0, nmin = 1 << 30, nmax = 0;
+    for (int i = 0; i < count; i++) {
+        const opo_ctx *c = ctxs[i];
+        if (!c)
+            return OPO_E_INVALID;
+        if (c->device != ctxs[0]->device || c->prec != ctxs[0]->prec)
+            return OPO_E_INVALID;
+        if (!c->have_crystal || !c->have_cavity)
+            return OPO_E_STATE;
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == c)
+                return OPO_E_INVALID;
+        fmax = std::max(fmax, c->F);
+        nmin = std::min(nmin, c->n);
+        nmax = std::max(nmax, c->n);
+    }
+    opo_batch *b = new (std::nothrow) opo_batch();
+    if (!b)
+        return OPO_E_NOMEM;
+    if (!fused_config(ctxs[0]->csz, fmax, nmin, nmax, cluster, 0, &b->cfg)) {
+        delete b;
+        return OPO_E_UNSUPPORTED;
+    }
+    b->ctxs.assign(ctxs, ctxs + count);
+    DeviceGuard g(ctxs[0]->device);
+    b->ev.resize(count);
+    for (int i = 0; i < count; i++)
+        cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
+    *out = b;
+    return OPO_OK;
+}
+
+int opo_batch_run(opo_batch *b, int64_t m)
+{
+    if (!b || m < 0)
+        return OPO_E_INVALID;
+    opo_ctx *c0 = b->ctxs[0];
+    DeviceGuard g(c0->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    cudaStream_t s = c0->stream;
+    const int count = (int)b->ctxs.size();
+    for (int i = 0; i < count; i++) {
+        opo_ctx *c = b->ctxs[i];
+        int rc = begin_call(c, m, b->cfg.cluster, false);
+        if (rc != OPO_OK)
+            return rc;
+        if (c->stream != s) {
+            cudaEventRecord(b->ev[i], c->stream);
+            cudaStreamWaitEvent(s, b->ev[i], 0);
+        }
+    }
+    int rc = m > 0 ? fused_run(b->ctxs.data(), count, b->cfg, m, s) : OPO_OK;
+    for (int i = 0; i < count && rc == OPO_OK; i++) {
+        opo_ctx *c = b->ctxs[i];
+        if (c->stream != s) {
+            cudaEventRecord(b->ev[i], s);
+            cudaStreamWaitEvent(c->stream, b->ev[i], 0);
+        }
+        c->rt += m;
+        c->last_M = m;
+        c->last_parts = b->cfg.cluster;
+        c->last_path = OPO_PATH_FUSED;
+        c->last_cluster = b->cfg.cluster;
+    }
+    return rc;
+}
+
+int opo_batch_destroy(opo_batch *b)
+{
+    if (!b)
+        return OPO_OK;
+    if (!b->ctxs.empty()) {
+        DeviceGuard g(b->ctxs[0]->device);
+        cudaStreamSynchronize(b->ctxs[0]->stream);
+        for (cudaEvent_t e : b->ev)
+            cudaEventDestroy(e);
+    }
+    delete b;
+    return OPO_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,280 @@
+// opo_common.cuh -- device building blocks shared by the plain and fused
+// split-step kernels: complex arithmetic on float2/double2, in-register DFTs
+// of radix 2..16, the radix plan of a Stockham FFT, and the nonlinear RK4
+// step of the coupled-wave equations (arXiv 2410.02532, Sec. 2.1 Eqs.
+// (CEp)-(CEi); Sec. 2.2 RK4 for the nonlinear half steps).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// ------------------------------------------------------------ complex ----
+
+template <class T> struct cvec;
+template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<double> { using type = double2; };
+template <class T> using cv = typename cvec<T>::type;
+
+template <class V> struct cscal;
+template <> struct cscal<float2> { using type = float; };
+template <> struct cscal<double2> { using type = double; };
+
+template <class V>
+__host__ __device__ __forceinline__ V cmk(typename cscal<V>::type re, typename cscal<V>::type im)
+{
+    V r;
+    r.x = re;
+    r.y = im;
+    return r;
+}
+template <class V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <class V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <class V> __device__ __forceinline__ V cmul(V a, V b)
+{
+    return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <class V> __device__ __forceinline__ V cmulc(V a, V b)
+{
+    return cmk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <class V> __device__ __forceinline__ V cconj(V a) { return cmk<V>(a.x, -a.y); }
+template <class V> __device__ __forceinline__ V cscale(V a, typename cscal<V>::type s)
+{
+    return cmk<V>(a.x * s, a.y * s);
+}
+// i * a
+template <class V> __device__ __forceinline__ V cmuli(V a) { return cmk<V>(-a.y, a.x); }
+template <class V> __device__ __forceinline__ typename cscal<V>::type cabs2(V a)
+{
+    return a.x * a.x + a.y * a.y;
+}
+
+// ------------------------------------------------- in-register DFTs ----
+// DFT of R values in natural order, X_k = sum_j v_j e^{DIR 2 pi i jk/R},
+// DIR = -1 forward, +1 inverse (unnormalized).  Recursive even/odd split
+// (radix-2 decimation in time); the constant twiddles are e^{DIR 2 pi i a/16}.
+
+template <int A, int DIR, class V>
+__device__ __forceinline__ V rot16(V x)
+{
+    // cos and sin of 2 pi a / 16, a = 0..7 (mathematical constants)
+    constexpr double c16[8] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
+                               0.38268343236508977173, 0.0, -0.38268343236508977173,
+                               -0.70710678118654752440, -0.92387953251128675613};
+    constexpr double s16[8] = {0.0, 0.38268343236508977173, 0.70710678118654752440,
+                               0.92387953251128675613, 1.0, 0.92387953251128675613,
+                               0.70710678118654752440, 0.38268343236508977173};
+    using S = typename cscal<V>::type;
+    if constexpr (A == 0) {
+        return x;
+    } else if constexpr (A == 4) {
+        return DIR < 0 ? cmk<V>(x.y, -x.x) : cmk<V>(-x.y, x.x);
+    } else {
+        const S c = (S)c16[A];
+        const S s = (S)(DIR * s16[A]);
+        return cmk<V>(x.x * c - x.y * s, x.x * s + x.y * c);
+    }
+}
+
+template <int R, int DIR, int K, class V>
+__device__ __forceinline__ void dft_combine(V *v, const V *e, const V *o)
+{
+    if constexpr (K < R / 2) {
+        V t = rot16<K * (16 / R), DIR>(o[K]);
+        v[K] = cadd(e[K], t);
+        v[K + R / 2] = csub(e[K], t);
+        dft_combine<R, DIR, K + 1>(v, e, o);
+    }
+}
+
+template <int R, int DIR, class V>
+__device__ __forceinline__ void dft(V *v)
+{
+    if constexpr (R == 1) {
+        return;
+    } else if constexpr (R == 2) {
+        V a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else {
+        V e[R / 2], o[R / 2];
+#pragma unroll
+        for (int j = 0; j < R / 2; j++) {
+            e[j] = v[2 * j];
+            o[j] = v[2 * j + 1];
+        }
+        dft<R / 2, DIR>(e);
+        dft<R / 2, DIR>(o);
+        dft_combine<R, DIR, 0>(v, e, o);
+    }
+}
+
+// ----------------------------------------------------- radix plan ----
+// A length L = 2^a transform runs as ceil(a/4) Stockham stages whose radices
+// (each 2..16) split the a bits as evenly as possible, largest first.
+struct RadixPlan {
+    int nst;       // number of stages
+    int lr[5];     // log2 radix of each stage
+};
+
+__host__ __device__ inline RadixPlan make_plan(int log2L)
+{
+    RadixPlan p;
+    p.nst = (log2L + 3) / 4;
+    if (p.nst == 0) {
+        return p;
+    }
+    int base = log2L / p.nst, extra = log2L % p.nst;
+    for (int s = 0; s < p.nst; s++)
+        p.lr[s] = base + (s < extra ? 1 : 0);
+    return p;
+}
+
+// ------------------------------------------------------------- RK4 ----
+// Pointwise right-hand side of the nonlinear part of Eqs. (CEp)-(CEi).
+// e = e^{+i dk z}.  Two-field (degenerate) form: f_p = i(kappa_p/2) A_s^2
+// e^{-i dk z}, f_s = i kappa_s A_p A_s* e^{+i dk z}.
+template <int F, class V>
+__device__ __forceinline__ void nl_rhs(const V *a, V e, const typename cscal<V>::type *kap,
+                                       bool use_e, V *f)
+{
+    if constexpr (F == 3) {
+        V sp = cmul(a[1], a[2]);        // A_s A_i
+        V ss = cmulc(a[0], a[2]);       // A_p A_i*
+        V si = cmulc(a[0], a[1]);       // A_p A_s*
+        if (use_e) {
+            sp = cmulc(sp, e);
+            ss = cmul(ss, e);
+            si = cmul(si, e);
+        }
+        f[0] = cscale(cmuli(sp), kap[0]);
+        f[1] = cscale(cmuli(ss), kap[1]);
+        f[2] = cscale(cmuli(si), kap[2]);
+    } else {
+        V sp = cmul(a[1], a[1]);        // A_s^2
+        V ss = cmulc(a[0], a[1]);       // A_p A_s*
+        if (use_e) {
+            sp = cmulc(sp, e);
+            ss = cmul(ss, e);
+        }
+        f[0] = cscale(cmuli(sp), kap[0] * (typename cscal<V>::type)0.5);
+        f[1] = cscale(cmuli(ss), kap[1]);
+    }
+}
+
+// One classic RK4 step of size h from z0: stage factors e0 = e^{i dk z0},
+// e1 = e^{i dk (z0 + h/2)}, e2 = e^{i dk (z0 + h)}.
+template <int F, class V>
+__device__ __forceinline__ void rk4_point(V *y, V e0, V e1, V e2,
+                                          const typename cscal<V>::type *kap,
+                                          typename cscal<V>::type h, bool use_e)
+{
+    using S = typename cscal<V>::type;
+    V k1[F], k2[F], k3[F], k4[F], t[F];
+    const S h2 = h * (S)0.5;
+    nl_rhs<F>(y, e0, kap, use_e, k1);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = cmk<V>(y[x].x + h2 * k1[x].x, y[x].y + h2 * k1[x].y);
+    nl_rhs<F>(t, e1, kap, use_e, k2);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = cmk<V>(y[x].x + h2 * k2[x].x, y[x].y + h2 * k2[x].y);
+    nl_rhs<F>(t, e1, kap, use_e, k3);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = cmk<V>(y[x].x + h * k3[x].x, y[x].y + h * k3[x].y);
+    nl_rhs<F>(t, e2, kap, use_e, k4);
+    const S h6 = h / (S)6;
+#pragma unroll
+    for (int x = 0; x < F; x++) {
+        S sx = k1[x].x + (S)2 * k2[x].x + (S)2 * k3[x].x + k4[x].x;
+        S sy = k1[x].y + (S)2 * k2[x].y + (S)2 * k3[x].y + k4[x].y;
+        y[x] = cmk<V>(y[x].x + h6 * sx, y[x].y + h6 * sy);
+    }
+}
+
+// --------------------------------------------------- shared context ----
+// Slots of the raw per-round-trip observable sums (FP64): Sum|A_x|^2 for
+// x = 0..2, Sum_k |X_k|^2 and Sum_k k'|X_k|^2 of the signal spectrum.
+#define OPO_NSLOT 5
+
+// ---------------------------------------------------- Stockham stage ----
+// One radix-R stage of a Stockham (autosort, decimation in time) transform
+// over nseq sequences of length L held in shared memory.  Butterfly j of a
+// sequence reads v_r = src[j + r L/R], multiplies by W_{Ns R}^{DIR r k}
+// (k = j mod Ns), takes an R-point DFT and stores output r at position
+// (j - k) R + k + r Ns.  After all stages the result is in natural order.
+// Element e of sequence seq lives at src[addr(seq, e)]; outputs go through
+// store(seq, e, value).  tw[i << twshift] = e^{-2 pi i i'/(Ns R)} ...: the
+// table holds W_M^i for a power-of-two M >= Ns R, and twshift = log2(M/(Ns R)).
+// SEQ_FAST: consecutive threads take consecutive sequences (column layouts);
+// otherwise consecutive butterflies of one sequence (row layouts).
+template <int R, int DIR, bool SEQ_FAST, class V, class Addr, class Store>
+__device__ __forceinline__ void stockham_stage(const V *__restrict__ src, int nseq, int L, int Ns,
+                                               Addr addr, Store store, const V *__restrict__ tw,
+                                               int twshift)
+{
+    const int Lr = L / R;
+    const int nbf = nseq * Lr;
+    for (int u = threadIdx.x; u < nbf; u += blockDim.x) {
+        int seq, j;
+        if (SEQ_FAST) {
+            seq = u % nseq;
+            j = u / nseq;
+        } else {
+            j = u % Lr;
+            seq = u / Lr;
+        }
+        const int k = j & (Ns - 1);
+        V v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            v[r] = src[addr(seq, j + r * Lr)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                V w = tw[(r * k) << twshift];
+                if (DIR > 0)
+                    w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft<R, DIR>(v);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            store(seq, base + r * Ns, v[r]);
+    }
+}
+
+// Dispatch a stage by log2 radix.
+template <int DIR, bool SEQ_FAST, class V, class Addr, class Store>
+__device__ __forceinline__ void stockham_stage_lr(int lr, const V *__restrict__ src, int nseq, int L,
+                                                  int Ns, Addr addr, Store store,
+                                                  const V *__restrict__ tw, int twshift)
+{
+    switch (lr) {
+    case 1:
+        stockham_stage<2, DIR, SEQ_FAST>(src, nseq, L, Ns, addr, store, tw, twshift);
+        break;
+    case 2:
+        stockham_stage<4, DIR, SEQ_FAST>(src, nseq, L, Ns, addr, store, tw, twshift);
+        break;
+    case 3:
+        stockham_stage<8, DIR, SEQ_FAST>(src, nseq, L, Ns, addr, store, tw, twshift);
+        break;
+    default:
+        stockham_stage<16, DIR, SEQ_FAST>(src, nseq, L, Ns, addr, store, tw, twshift);
+        break;
+    }
+}
+
+__host__ __device__ inline int ilog2(unsigned v)
+{
+    int r = 0;
+    while ((1u << r) < v)
+        r++;
+    return r;
+}

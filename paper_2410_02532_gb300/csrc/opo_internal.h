@@ -1,0 +1,106 @@
+// opo_internal.h -- host-side state of a libopo context and the launchers
+// that the C-ABI file (opo_abi.cu) calls in the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/opo.h"
+
+namespace opo {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kEps0 = 8.8541878128e-12; // vacuum permittivity [F/m]
+constexpr double kC0 = 299792458.0;        // speed of light [m/s]
+constexpr int kNslot = 5;                  // raw observable sums per round trip
+
+// Device control block read by every per-round-trip kernel, so that one
+// captured graph serves every round trip of a call.
+struct DevCtl {
+    int64_t rt0;      // absolute round-trip index of slot 0 of the current call
+    int64_t slot;     // round trip within the current call
+    double *obs;      // raw sums [slot][parts][kNslot]
+    int32_t parts;    // partial sums per slot (CTAs per instance; 1 on the plain path)
+    int32_t err;      // sticky error word: 1 = non-finite field
+};
+
+// Scalars of one instance derived once on the host from crystal and cavity.
+struct Derived {
+    double kappa[3];     // 2 pi d_eff / (n lambda)
+    double dz, h;        // step and RK4 half step
+    double bc_re[3], bc_im[3]; // sqrt(R) e^{i delta} for resonant fields, 1 otherwise
+    double outscale[3];  // sqrt(1 - R) for resonant fields, 1 otherwise
+    double pscale[3];    // n eps0 c / 2 * pi w0^2
+    bool use_dk;
+    bool eom;
+};
+
+struct FusedCfg {
+    int cluster;         // CTAs per instance
+    int threads;         // threads per CTA
+    int rt_per_launch;   // round trips per launch
+    bool disp_in_smem;   // dispersion factors resident in shared memory
+    size_t smem;         // dynamic shared memory per CTA
+};
+
+} // namespace opo
+
+struct opo_ctx {
+    opo_grid grid;
+    opo_crystal crystal;
+    opo_cavity cavity;
+    bool have_crystal = false, have_cavity = false;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t capture_stream = nullptr;
+    int n = 0, logn = 0, F = 0, prec = 0;
+    size_t csz = 0; // bytes per complex element
+    // device memory (complex arrays in the context's precision)
+    void *d_fields = nullptr;  // F*N intracavity state
+    void *d_out = nullptr;     // F*N output-coupled fields of the last round trip
+    void *d_scratch = nullptr; // F*N FFT intermediate of the plain path
+    void *d_pump = nullptr;    // N input pump
+    void *d_disp = nullptr;    // F*N dispersion factors / N, natural order
+    void *d_gdd = nullptr;     // F*N cavity spectral factors / N, natural order
+    void *d_tw = nullptr;      // N twiddles W_N^j = e^{-2 pi i j/N}
+    void *d_ekz = nullptr;     // 4 nz + 1 factors e^{i dk q dz/4}
+    int ekz_cap = 0;
+    double *d_pump_user = nullptr; // staging for OPO_PUMP_USER (FP64)
+    double *d_stage = nullptr;     // 2N doubles: host <-> device field staging
+    double *d_obs = nullptr;   // raw observable sums
+    double *d_trace = nullptr; // rows {P_p, P_s, P_i, nu_c}
+    int64_t obs_cap = 0;       // capacity in round trips (times parts)
+    int obs_parts_cap = 0;
+    opo::DevCtl *d_ctl = nullptr;
+    double *h_pinned = nullptr; // small pinned staging
+    int64_t rt = 0;            // round-trip counter m
+    int64_t last_M = 0;        // round trips in the last call
+    int last_parts = 1;
+    opo::Derived dv{};
+    int path_req = OPO_PATH_AUTO, cluster_req = 0, rtpl_req = 0;
+    int last_path = OPO_PATH_PLAIN, last_cluster = 0;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+};
+
+namespace opo {
+
+// opo_setup.cu
+int setup_twiddles(opo_ctx *c);
+int setup_crystal_tables(opo_ctx *c);
+int setup_cavity_tables(opo_ctx *c);
+int finalize_trace(opo_ctx *c, int64_t M, int parts);
+
+// opo_plain.cu
+void plain_prepare(opo_ctx *c);
+int plain_enqueue_roundtrip(opo_ctx *c, cudaStream_t s);
+
+// opo_fused.cu: a cluster configuration able to hold instances with up to
+// fmax fields and nmin..nmax points (false if none fits or can launch).
+bool fused_config(size_t csz, int fmax, int nmin, int nmax, int cluster_req, int rtpl_req,
+                  FusedCfg *out);
+int fused_max_active(bool dbl, int cluster, size_t smem);
+int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s);
+
+} // namespace opo

@@ -1,0 +1,278 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+"Per pass" parity: the GPU and the oracle start a round trip from the same
+stored state and their results are compared element by element (relative L2
+per field): FP64 path <= 1e-10, FP32 fields with FP64 phases <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2410_02532_gb300 import opo
+from paper_2410_02532_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {opo.OPO_FP64: 1e-10, opo.OPO_FP32_PH64: 1e-4}
+PRECS = [opo.OPO_FP64, opo.OPO_FP32_PH64]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2410_02532_gb300 import build
+    build.build()
+    opo.lib()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_rt(cfg, fields, m0=0, M=1, tod_div=6.0):
+    p = orc.params(cfg, tod_div=tod_div)
+    pump = orc.pump_profile(p, cfg.pump_kind, cfg.pump_power, cfg.pump_fwhm)
+    out, trace, outf, st = orc.run(p, fields, pump, m0, M)
+    assert st == 0
+    return out, outf, trace
+
+
+def gpu_rt(cfg, fields, prec, path, cluster=0, m0=0, M=1, tod_div=0.0, rtpl=0):
+    with opo.Context(cfg, precision=prec, fields=fields, tod_div=tod_div) as ctx:
+        ctx.set_fields(fields, rt_index=m0)
+        ctx.set_path(path, cluster, rtpl)
+        s = ctx.run(M)
+        return ctx.get_fields(), ctx.get_fields(opo.OPO_OUTPUT), ctx.trace(M), s
+
+
+def spectral_width(cfg, a):
+    X = np.abs(np.fft.fft(a)) ** 2
+    f = np.fft.fftfreq(cfg.n, cfg.t_window / cfg.n)
+    mu = np.sum(f * X) / np.sum(X)
+    return float(np.sqrt(np.sum((f - mu) ** 2 * X) / np.sum(X)))
+
+
+def compare(cfg, got, ref, prec, what=""):
+    tol = TOL[prec]
+    g_f, g_o, g_t = got[:3]
+    r_f, r_o, r_t = ref
+    for x in range(cfg.nfields):
+        e = rel_l2(g_f[x], r_f[x])
+        assert e <= tol, (what, "field", x, e)
+        e = rel_l2(g_o[x], r_o[x])
+        assert e <= tol, (what, "output", x, e)
+    for x in range(cfg.nfields):
+        assert abs(g_t[-1, x] - r_t[-1, x]) <= 4 * tol * abs(r_t[-1, x]) + 1e-300, (what, "P", x)
+    w = max(spectral_width(cfg, r_o[1]), 0.5 / cfg.t_window)
+    assert abs(g_t[-1, 3] - r_t[-1, 3]) <= 4 * tol * w, (what, "centroid")
+
+
+def strong(cfg, amp=3e6, seed_off=0):
+    a = cfg.initial_fields()
+    for x in range(1, cfg.nfields):
+        a[x] = a[x] + W.noise(cfg.n, amp, cfg.seed + 17 + seed_off, cfg.instance, x)
+    return a
+
+
+# ------------------------------------------------------------ workloads
+
+def cfg_small_sro():
+    return W.cw_sro_1024()
+
+
+def cfg_dispersive(n=1024, nz=20):
+    c = W.cw_sro_16k()
+    return c.replace(n=n, nz=nz, name="dispersive")
+
+
+def cfg_sync(n=2048):
+    c = W.sync_pumped_64k(delay_fs=10.0)
+    return c.replace(n=n, nz=16, t_window=20e-12, t_rt=20e-12, eom_f=1.0 / 20e-12,
+                     name="sync")
+
+
+def cfg_degenerate(n=256):
+    return W.degenerate_2field(n=n, level=3.0).replace(dk=150.0, nz=30)
+
+
+def cfg_dro(n=512):
+    c = W.OPOConfig(n=n, nz=25, resonant_mask=0b110, R=(0.0, 0.95, 0.9),
+                    delta=(0.0, 0.3, -0.2), alpha=(1.0, 2.0, 3.0), dk=80.0,
+                    dbeta1=(1e-10, 0.0, -5e-11), beta2=(3.8e-25, 1.1e-25, -7.5e-25),
+                    name="dro")
+    return c.replace(pump_power=3.0 * W.sro_threshold_power(c))
+
+
+CASES = {
+    "sro1024": (cfg_small_sro, 3e6),
+    "sro1024_noise": (cfg_small_sro, 0.0),
+    "dispersive": (cfg_dispersive, 3e6),
+    "sync_eom_delay": (cfg_sync, 1e6),
+    "degenerate": (cfg_degenerate, 1e6),
+    "dro_loss_dk": (cfg_dro, 2e6),
+    "tiny16": (lambda: cfg_dro(n=16), 2e6),
+}
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=["fp64", "fp32ph64"])
+@pytest.mark.parametrize("path", [opo.OPO_PATH_PLAIN, opo.OPO_PATH_FUSED], ids=["plain", "fused"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_one_round_trip(case, path, prec):
+    make, amp = CASES[case]
+    cfg = make()
+    a0 = strong(cfg, amp) if amp > 0 else cfg.initial_fields()
+    m0 = 3
+    ref = oracle_rt(cfg, a0, m0=m0)
+    got = gpu_rt(cfg, a0, prec, path, m0=m0)
+    compare(cfg, got, ref, prec, case)
+    assert got[3].path == path
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8, 16])
+def test_fused_cluster_sizes(cluster):
+    cfg = cfg_dispersive(n=4096, nz=8)
+    a0 = strong(cfg)
+    ref = oracle_rt(cfg, a0)
+    for prec in PRECS:
+        try:
+            got = gpu_rt(cfg, a0, prec, opo.OPO_PATH_FUSED, cluster=cluster)
+        except opo.OPOError as e:
+            assert e.status == opo.OPO_E_UNSUPPORTED
+            continue
+        compare(cfg, got, ref, prec, "C=%d" % cluster)
+        assert got[3].cluster == cluster
+
+
+def test_tod_divisor_three():
+    cfg = cfg_dispersive(n=512, nz=10).replace(beta3=(2.5e-39, 2.5e-39, 2.5e-39))
+    a0 = strong(cfg)
+    ref = oracle_rt(cfg, a0, tod_div=3.0)
+    got = gpu_rt(cfg, a0, opo.OPO_FP64, opo.OPO_PATH_FUSED, tod_div=3.0)
+    compare(cfg, got, ref, opo.OPO_FP64, "tod3")
+
+
+@pytest.mark.parametrize("path", [opo.OPO_PATH_PLAIN, opo.OPO_PATH_FUSED], ids=["plain", "fused"])
+def test_per_pass_chain(path):
+    """Four round trips, each compared from the GPU's own previous state."""
+    cfg = cfg_dispersive(n=1024, nz=10)
+    a = strong(cfg)
+    with opo.Context(cfg, precision=opo.OPO_FP32_PH64, fields=a) as ctx:
+        ctx.set_path(path)
+        for m in range(4):
+            start = ctx.get_fields()
+            ctx.run(1)
+            got = ctx.get_fields()
+            ref, _, _ = oracle_rt(cfg, start, m0=m)
+            for x in range(cfg.nfields):
+                assert rel_l2(got[x], ref[x]) <= 1e-4
+
+
+def test_resume_is_bitwise():
+    """M straight through equals M1, then M2 from the stored state."""
+    cfg = cfg_sync(n=1024)
+    a = strong(cfg)
+    for path in (opo.OPO_PATH_PLAIN, opo.OPO_PATH_FUSED):
+        with opo.Context(cfg, fields=a) as c1:
+            c1.set_path(path, 0, 2)
+            c1.run(5)
+            f1 = c1.get_fields()
+            t1 = c1.trace(5)
+        with opo.Context(cfg, fields=a) as c2:
+            c2.set_path(path, 0, 2)
+            c2.run(2)
+            mid = c2.get_fields()
+        with opo.Context(cfg, fields=mid) as c3:
+            c3.set_fields(mid, rt_index=2)
+            c3.set_path(path, 0, 2)
+            c3.run(3)
+            f3 = c3.get_fields()
+            t3 = c3.trace(3)
+        assert np.array_equal(f1, f3)
+        assert np.array_equal(t1[2:], t3)
+
+
+def test_batch_matches_alone_bitwise():
+    cfgs = [cfg_dispersive(n=1024, nz=8), cfg_dro(n=2048).replace(nz=8),
+            cfg_degenerate(n=4096).replace(nz=8)]
+    starts = [strong(c) for c in cfgs]
+    alone = []
+    for c, a in zip(cfgs, starts):
+        with opo.Context(c, fields=a) as ctx:
+            ctx.set_path(opo.OPO_PATH_FUSED, 4)
+            ctx.run(3)
+            alone.append((ctx.get_fields(), ctx.trace(3)))
+    ctxs = [opo.Context(c, fields=a) for c, a in zip(cfgs, starts)]
+    try:
+        b = opo.opo_batch_create([c.h for c in ctxs], 4)
+        opo.opo_batch_run(b, 3)
+        for ctx, (f, t) in zip(ctxs, alone):
+            assert np.array_equal(ctx.get_fields(), f)
+            assert np.array_equal(ctx.trace(3), t)
+        opo.opo_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_nonfinite_is_reported():
+    cfg = W.OPOConfig(n=64, nz=1, length=0.5, pump_power=1e12)
+    a = strong(cfg, 1e8)
+    for path in (opo.OPO_PATH_PLAIN, opo.OPO_PATH_FUSED):
+        with opo.Context(cfg, fields=a) as ctx:
+            ctx.set_path(path)
+            with pytest.raises(opo.OPOError) as ei:
+                ctx.run(50)
+            assert ei.value.status == opo.OPO_E_NONFINITE
+
+
+def test_state_errors():
+    cfg = cfg_small_sro()
+    h = opo.opo_create(opo.grid_from(cfg))
+    try:
+        with pytest.raises(opo.OPOError) as ei:
+            opo.opo_run_roundtrips(h, 1)
+        assert ei.value.status == opo.OPO_E_STATE
+        with pytest.raises(opo.OPOError):
+            opo.opo_set_fields(h, 3, np.zeros(cfg.n))
+        with pytest.raises(opo.OPOError):
+            opo.opo_set_fields(h, 0, np.zeros(cfg.n - 1))
+    finally:
+        opo.opo_destroy(h)
+
+
+def test_device_field_transfer():
+    torch = pytest.importorskip("torch")
+    cfg = cfg_small_sro()
+    a = strong(cfg)
+    with opo.Context(cfg, precision=opo.OPO_FP32_PH64, fields=a) as ctx:
+        t = torch.zeros(cfg.n, dtype=torch.complex64, device="cuda")
+        opo.opo_get_fields_device(ctx.h, 1, opo.OPO_INTRACAVITY, t.data_ptr(), cfg.n)
+        ctx.sync()
+        assert np.allclose(t.cpu().numpy(), a[1].astype(np.complex64))
+        t2 = t * 2
+        torch.cuda.synchronize()
+        opo.opo_set_fields_device(ctx.h, 1, t2.data_ptr(), cfg.n)
+        ctx.sync()
+        assert np.allclose(ctx.get_fields()[1], 2 * a[1].astype(np.complex64))
+
+
+# ------------------------------------------------ full-size workloads
+
+def test_full_size_n16384_round_trip():
+    """The 2^14-point, 100-step, GVM/GVD/TOD/GDD workload: one round trip of
+    the fused FP32+FP64-phase path (the benchmarked configuration) and of the
+    FP64 path, each against the oracle."""
+    cfg = W.cw_sro_16k()
+    a0 = strong(cfg)
+    ref = oracle_rt(cfg, a0, m0=7)
+    got = gpu_rt(cfg, a0, opo.OPO_FP32_PH64, opo.OPO_PATH_AUTO, m0=7)
+    compare(cfg, got, ref, opo.OPO_FP32_PH64, "n16384 fp32")
+    got = gpu_rt(cfg, a0, opo.OPO_FP64, opo.OPO_PATH_AUTO, m0=7)
+    compare(cfg, got, ref, opo.OPO_FP64, "n16384 fp64")
+
+
+def test_full_size_n65536_round_trip():
+    cfg = W.sync_pumped_64k(delay_fs=-20.0)
+    a0 = strong(cfg, 1e6)
+    ref = oracle_rt(cfg, a0, m0=1)
+    got = gpu_rt(cfg, a0, opo.OPO_FP32_PH64, opo.OPO_PATH_AUTO, m0=1)
+    compare(cfg, got, ref, opo.OPO_FP32_PH64, "n65536")
