@@ -224,6 +224,33 @@ OPO_API int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t coun
 OPO_API int opo_batch_run(opo_batch *batch, int64_t m);
 OPO_API int opo_batch_destroy(opo_batch *batch);
 
+/* One crystal pass without any device allocation, for callers that cannot
+ * call cudaMalloc (code that runs inside another framework's memory pool or
+ * under an allocator that is locked down or already exhausted).  The paper
+ * has no counterpart; it is the crystal pass of opo_run_roundtrips (plain
+ * path) without a context.
+ *
+ * fields: device pointer to grid->nfields x grid->n complex values in the
+ *         grid's precision (float2 for OPO_FP32_PH64, double2 for OPO_FP64),
+ *         field-major, advanced in place by crystal->nz symmetrized steps.
+ * stream: cudaStream_t to enqueue on (NULL = legacy default stream); the call
+ *         returns without synchronizing; grid->stream is ignored.
+ * Scratch: a fixed 4 MiB device array inside the library, shared by every
+ *         call on a device and held by every GPU that loads the library until
+ *         the process exits.  It needs
+ *         bytes(c) = round256(c N) + 2 round256(c F N) + round256(c (4 nz + 1))
+ *         <= 4 MiB with c = 8 (FP32) or 16 (FP64), e.g. N <= 2^15 with 3
+ *         fields in FP64, N <= 2^16 in FP32; larger requests return
+ *         OPO_E_INVALID without launching anything.  Every call rewrites all
+ *         of the scratch it reads (nothing must start at zero).  Calls whose
+ *         work overlaps on the GPU (other streams, other threads) race on the
+ *         shared scratch: serialize them.
+ * Set-up: the first call on a device looks up the array's device address with
+ *         that device current (no allocation); make that first call before any
+ *         stream capture. */
+OPO_API int opo_crystal_pass_noalloc(const opo_grid *grid, const opo_crystal *crystal,
+                                     void *fields, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

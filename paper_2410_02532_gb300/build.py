@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libopo.so")
-SOURCES = ["opo_abi.cu", "opo_setup.cu", "opo_plain.cu", "opo_fused.cu"]
+SOURCES = ["opo_abi.cu", "opo_setup.cu", "opo_plain.cu", "opo_fused.cu", "opo_noalloc.cu"]
 HEADERS = ["opo_common.cuh", "opo_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

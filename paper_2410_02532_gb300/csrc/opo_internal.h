@@ -91,10 +91,17 @@ int setup_twiddles(opo_ctx *c);
 int setup_crystal_tables(opo_ctx *c);
 int setup_cavity_tables(opo_ctx *c);
 int finalize_trace(opo_ctx *c, int64_t M, int parts);
+// twiddles, dispersion factors and e^{i dk q dz/4} into caller-given buffers
+int setup_pass_tables(void *tw, void *disp, void *ekz, int n, int F, bool dbl,
+                      const opo_crystal &k, double t_window, cudaStream_t s);
 
 // opo_plain.cu
 void plain_prepare(opo_ctx *c);
 int plain_enqueue_roundtrip(opo_ctx *c, cudaStream_t s);
+// one crystal pass of the plain kernels on caller-given buffers
+int plain_pass_raw(void *fields, void *scratch, const void *tw, const void *disp, const void *ekz,
+                   int n, int F, int nz, const double kappa[3], double h, bool use_dk, bool dbl,
+                   cudaStream_t st);
 
 // opo_fused.cu: a cluster configuration able to hold instances with up to
 // fmax fields and nmin..nmax points (false if none fits or can launch).

@@ -1,0 +1,110 @@
+// opo_noalloc.cu -- opo_crystal_pass_noalloc: one crystal pass of the plain
+// kernels on caller-owned device fields, for callers that cannot allocate
+// device memory (for example code running inside another framework's memory
+// pool, or a process whose allocator is locked down).  Its scratch (FFT
+// intermediate, twiddles, dispersion factors, e^{i dk z} factors) lives in
+// one file-scope device array, so the call itself allocates nothing.
+#include <cmath>
+#include <mutex>
+
+#include "opo_common.cuh"
+#include "opo_internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(4) << 20; // 4 MiB
+constexpr int kMaxDevices = 64;
+
+// Shared by every call on a device; every GPU that loads the library holds it
+// until the process exits.
+static __device__ __align__(256) unsigned char opo_noalloc_scratch[kScratchBytes];
+
+// Device address of the array, found once per device with that device
+// current (the host-side name of a __device__ array is only a stand-in).
+void *g_scratch_ptr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
+
+int scratch_for(int dev, void **out)
+{
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, opo_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return OPO_E_CUDA;
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return OPO_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+} // namespace
+
+extern "C" OPO_API int opo_crystal_pass_noalloc(const opo_grid *grid, const opo_crystal *k,
+                                                void *fields, void *stream)
+{
+    if (!grid || !k || !fields)
+        return OPO_E_INVALID;
+    const int n = grid->n;
+    if (n < 16 || n > (1 << 17) || (n & (n - 1)) != 0)
+        return OPO_E_INVALID;
+    if (grid->nfields != 2 && grid->nfields != 3)
+        return OPO_E_INVALID;
+    if (grid->precision != OPO_FP64 && grid->precision != OPO_FP32_PH64)
+        return OPO_E_INVALID;
+    if (!(grid->t_window_s > 0.0) || !std::isfinite(grid->t_window_s))
+        return OPO_E_INVALID;
+    if (!(k->length_m > 0.0) || !std::isfinite(k->length_m) || k->nz < 1 || k->nz > 100000 ||
+        !std::isfinite(k->dk_per_m) || !std::isfinite(k->deff_mpv))
+        return OPO_E_INVALID;
+    const int F = grid->nfields;
+    for (int x = 0; x < F; x++)
+        if (!(k->lambda_m[x] > 0.0) || !(k->n[x] > 0.0) || !std::isfinite(k->lambda_m[x]) ||
+            !std::isfinite(k->n[x]) || !std::isfinite(k->alpha_per_m[x]) ||
+            !std::isfinite(k->dbeta1_s_per_m[x]) || !std::isfinite(k->beta2_s2_per_m[x]) ||
+            !std::isfinite(k->beta3_s3_per_m[x]))
+            return OPO_E_INVALID;
+    const bool dbl = grid->precision == OPO_FP64;
+    const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
+    // scratch layout: twiddles N | FFT intermediate F*N | dispersion F*N | ekz 4 nz + 1
+    const size_t b_tw = align256(csz * n);
+    const size_t b_scr = align256(csz * (size_t)F * n);
+    const size_t b_disp = align256(csz * (size_t)F * n);
+    const size_t b_ekz = align256(csz * (size_t)(4 * k->nz + 1));
+    if (b_tw + b_scr + b_disp + b_ekz > kScratchBytes)
+        return OPO_E_INVALID; // beyond the fixed scratch: use the context API
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return OPO_E_CUDA;
+    }
+    if (grid->device < 0 || grid->device >= ndev || grid->device >= kMaxDevices)
+        return OPO_E_INVALID;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess)
+        prev = -1;
+    if (cudaSetDevice(grid->device) != cudaSuccess)
+        return OPO_E_CUDA;
+    void *base = nullptr;
+    int rc = scratch_for(grid->device, &base);
+    if (rc == OPO_OK) {
+        cudaStream_t s = (cudaStream_t)stream;
+        char *b = (char *)base;
+        void *tw = b, *scr = b + b_tw, *disp = b + b_tw + b_scr, *ekz = b + b_tw + b_scr + b_disp;
+        rc = opo::setup_pass_tables(tw, disp, ekz, n, F, dbl, *k, grid->t_window_s, s);
+        if (rc == OPO_OK) {
+            double kappa[3] = {0.0, 0.0, 0.0};
+            for (int x = 0; x < F; x++)
+                kappa[x] = 2.0 * opo::kPi * k->deff_mpv / (k->n[x] * k->lambda_m[x]);
+            const double h = 0.5 * k->length_m / (double)k->nz;
+            rc = opo::plain_pass_raw(fields, scr, tw, disp, ekz, n, F, k->nz, kappa, h,
+                                     k->dk_per_m != 0.0, dbl, s);
+        }
+    }
+    if (prev >= 0)
+        cudaSetDevice(prev);
+    return rc;
+}

@@ -275,6 +275,22 @@ struct PlainFFT {
         smr = (size_t)2 * Br * (Q + 1) * sizeof(cv<T>);
         tw = (const cv<T> *)c->d_tw;
     }
+    // the same plan for caller-given sizes and twiddle table
+    void init_raw(int n_, int logn_, const cv<T> *tw_)
+    {
+        n = n_;
+        logn = logn_;
+        logP = logn / 2;
+        logQ = logn - logP;
+        P = 1 << logP;
+        Q = 1 << logQ;
+        int seg = (sizeof(T) == 8) ? 4 : 8;
+        Bc = Q < seg ? Q : seg;
+        Br = P < seg ? P : seg;
+        smc = (size_t)2 * Bc * P * sizeof(cv<T>);
+        smr = (size_t)2 * Br * (Q + 1) * sizeof(cv<T>);
+        tw = tw_;
+    }
     // transform `count` consecutive fields of `a` in place, scratch `s`
     template <int DIR>
     void run(cv<T> *a, cv<T> *s, int count, cudaStream_t st) const
@@ -377,6 +393,49 @@ void plain_prepare(opo_ctx *c)
 int plain_enqueue_roundtrip(opo_ctx *c, cudaStream_t s)
 {
     return c->prec == OPO_FP64 ? enqueue_rt<double>(c, s) : enqueue_rt<float>(c, s);
+}
+
+namespace {
+
+// The crystal pass alone (nz symmetrized steps) on caller-provided buffers.
+template <class T>
+int pass_raw(void *fields, void *scratch, const void *tw, const void *disp, const void *ekz,
+             int n, int F, int nz, const double kappa[3], double h, bool use_dk, cudaStream_t st)
+{
+    using V = cv<T>;
+    prepare<T>();
+    V *fld = (V *)fields;
+    V *scr = (V *)scratch;
+    PlainFFT<T> fft;
+    fft.init_raw(n, ilog2((unsigned)n), (const V *)tw);
+    const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
+    for (int j = 0; j < nz; j++) {
+        for (int half = 0; half < 2; half++) {
+            int q0 = 4 * j + 2 * half;
+            if (F == 3)
+                k_rk4<T, 3><<<gN, kThreads, 0, st>>>(fld, n, (const V *)ekz, q0, (T)h, (T)kappa[0],
+                                                     (T)kappa[1], (T)kappa[2], use_dk);
+            else
+                k_rk4<T, 2><<<gN, kThreads, 0, st>>>(fld, n, (const V *)ekz, q0, (T)h, (T)kappa[0],
+                                                     (T)kappa[1], (T)kappa[2], use_dk);
+            if (half == 0) {
+                fft.template run<-1>(fld, scr, F, st);
+                k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)disp, F * n);
+                fft.template run<1>(fld, scr, F, st);
+            }
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
+}
+
+} // namespace
+
+int plain_pass_raw(void *fields, void *scratch, const void *tw, const void *disp, const void *ekz,
+                   int n, int F, int nz, const double kappa[3], double h, bool use_dk, bool dbl,
+                   cudaStream_t st)
+{
+    return dbl ? pass_raw<double>(fields, scratch, tw, disp, ekz, n, F, nz, kappa, h, use_dk, st)
+               : pass_raw<float>(fields, scratch, tw, disp, ekz, n, F, nz, kappa, h, use_dk, st);
 }
 
 } // namespace opo

@@ -195,6 +195,32 @@ int setup_cavity_tables(opo_ctx *c)
     return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
 }
 
+int setup_pass_tables(void *tw, void *disp, void *ekz, int n, int F, bool dbl,
+                      const opo_crystal &k, double t_window, cudaStream_t s)
+{
+    DispArgs a;
+    for (int x = 0; x < 3; x++) {
+        a.alpha[x] = k.alpha_per_m[x];
+        a.db1[x] = k.dbeta1_s_per_m[x];
+        a.b2[x] = k.beta2_s2_per_m[x];
+        a.b3[x] = k.beta3_s3_per_m[x];
+    }
+    a.tod_div = k.tod_div > 0.0 ? k.tod_div : 6.0;
+    a.dz = k.length_m / (double)k.nz;
+    a.t_window = t_window;
+    const int cnt = 4 * k.nz + 1;
+    if (dbl) {
+        k_twiddles<double><<<grid_for(n), 256, 0, s>>>((double2 *)tw, n);
+        k_disp_table<double><<<grid_for((int64_t)F * n), 256, 0, s>>>((double2 *)disp, n, F, a);
+        k_ekz_table<double><<<grid_for(cnt), 256, 0, s>>>((double2 *)ekz, cnt, k.dk_per_m, a.dz);
+    } else {
+        k_twiddles<float><<<grid_for(n), 256, 0, s>>>((float2 *)tw, n);
+        k_disp_table<float><<<grid_for((int64_t)F * n), 256, 0, s>>>((float2 *)disp, n, F, a);
+        k_ekz_table<float><<<grid_for(cnt), 256, 0, s>>>((float2 *)ekz, cnt, k.dk_per_m, a.dz);
+    }
+    return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
+}
+
 int finalize_trace(opo_ctx *c, int64_t M, int parts)
 {
     if (M <= 0)
