@@ -213,13 +213,16 @@ OPO_API int opo_destroy(opo_ctx *ctx);
 /* Static string for a status code. */
 OPO_API const char *opo_status_string(int status);
 
-/* Batched sweep: many instances in one fused launch, one thread-block cluster
- * per instance.  All contexts must be on one device, in one precision, with
- * crystal and cavity set; N, field count, nz and every parameter may differ.
- * The batch keeps pointers to the contexts (which stay owned by the caller
- * and must outlive the batch) and runs on the first context's stream.
- * Each instance advances exactly as opo_run_roundtrips would advance it on
- * the fused path with the same cluster size. */
+/* Batched sweep: many instances advanced together on the fused path, one
+ * thread-block cluster per instance.  Instances are grouped by (N, field
+ * count); each group is one persistent launch and the groups run
+ * concurrently.  All contexts must be on one device, in one precision, with
+ * crystal and cavity set; every other parameter may differ.  The batch keeps
+ * pointers to the contexts (owned by the caller; they must outlive the batch)
+ * and is ordered on the first context's stream.  Each instance advances
+ * bit-for-bit as opo_run_roundtrips would advance it alone on the fused path
+ * with the same cluster size (cluster = 0: each group's default).
+ * OPO_E_UNSUPPORTED if some group cannot run with that cluster size. */
 OPO_API int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster);
 OPO_API int opo_batch_run(opo_batch *batch, int64_t m);
 OPO_API int opo_batch_destroy(opo_batch *batch);

@@ -240,7 +240,7 @@ int choose_path(opo_ctx *c, FusedCfg *cfg)
 {
     if (c->path_req == OPO_PATH_PLAIN)
         return OPO_PATH_PLAIN;
-    bool ok = fused_config(c->csz, c->F, c->n, c->n, c->cluster_req, c->rtpl_req, cfg);
+    bool ok = fused_config(c->csz, c->F, c->F, c->n, c->n, c->cluster_req, c->rtpl_req, cfg);
     if (c->path_req == OPO_PATH_FUSED)
         return ok ? OPO_PATH_FUSED : -1;
     return ok ? OPO_PATH_FUSED : OPO_PATH_PLAIN;
@@ -514,7 +514,7 @@ int opo_set_path(opo_ctx *c, int32_t path, int32_t cluster, int32_t rt_per_launc
         return OPO_E_INVALID;
     if (path == OPO_PATH_FUSED) {
         FusedCfg cfg;
-        if (!fused_config(c->csz, c->F, c->n, c->n, cluster, rt_per_launch, &cfg))
+        if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, rt_per_launch, &cfg))
             return OPO_E_UNSUPPORTED;
     }
     c->path_req = path;
@@ -608,9 +608,9 @@ int opo_fused_capacity(const opo_ctx *c, int32_t cluster, int32_t *max_active,
     if (!g.ok)
         return OPO_E_CUDA;
     FusedCfg cfg;
-    if (!fused_config(c->csz, c->F, c->n, c->n, cluster, 0, &cfg))
+    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, &cfg))
         return OPO_E_UNSUPPORTED;
-    *max_active = fused_max_active(c->prec == OPO_FP64, cfg.cluster, cfg.smem);
+    *max_active = fused_max_active(c->prec == OPO_FP64, c->F, c->n, cfg);
     if (cluster_out)
         *cluster_out = cfg.cluster;
     return OPO_OK;
@@ -626,11 +626,39 @@ int opo_sync(opo_ctx *c)
 
 } // extern "C"
 
+// A batch is split into groups of equal (N, field count); each group runs
+// as one fused launch with the configuration a lone instance of that group
+// would get for the requested cluster size, so every instance advances
+// bit-for-bit as it would alone.  Groups run concurrently on forked streams.
+struct BatchGroup {
+    std::vector<opo_ctx *> ctxs;
+    FusedCfg cfg{};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
 struct opo_batch {
     std::vector<opo_ctx *> ctxs;
-    FusedCfg cfg;
-    std::vector<cudaEvent_t> ev;
+    std::vector<BatchGroup> groups;
+    std::vector<cudaEvent_t> ev; // one per context: stream ordering
+    cudaEvent_t fork = nullptr;
 };
+
+static void batch_free(opo_batch *b)
+{
+    for (BatchGroup &g : b->groups) {
+        if (g.stream)
+            cudaStreamDestroy(g.stream);
+        if (g.done)
+            cudaEventDestroy(g.done);
+    }
+    for (cudaEvent_t e : b->ev)
+        if (e)
+            cudaEventDestroy(e);
+    if (b->fork)
+        cudaEventDestroy(b->fork);
+    delete b;
+}
 
 extern "C" {
 
@@ -643,7 +671,6 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
         return OPO_E_INVALID;
     if (cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)))
         return OPO_E_INVALID;
-    int fmax = 0, nmin = 1 << 30, nmax = 0;
     for (int i = 0; i < count; i++) {
         const opo_ctx *c = ctxs[i];
         if (!c)
@@ -655,22 +682,49 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
         for (int j = 0; j < i; j++)
             if (ctxs[j] == c)
                 return OPO_E_INVALID;
-        fmax = std::max(fmax, c->F);
-        nmin = std::min(nmin, c->n);
-        nmax = std::max(nmax, c->n);
     }
+    DeviceGuard g(ctxs[0]->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
     opo_batch *b = new (std::nothrow) opo_batch();
     if (!b)
         return OPO_E_NOMEM;
-    if (!fused_config(ctxs[0]->csz, fmax, nmin, nmax, cluster, 0, &b->cfg)) {
-        delete b;
-        return OPO_E_UNSUPPORTED;
-    }
     b->ctxs.assign(ctxs, ctxs + count);
-    DeviceGuard g(ctxs[0]->device);
-    b->ev.resize(count);
-    for (int i = 0; i < count; i++)
-        cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < count; i++) {
+        opo_ctx *c = ctxs[i];
+        int gi = -1;
+        for (size_t k = 0; k < b->groups.size(); k++)
+            if (b->groups[k].ctxs[0]->n == c->n && b->groups[k].ctxs[0]->F == c->F)
+                gi = (int)k;
+        if (gi < 0) {
+            b->groups.emplace_back();
+            gi = (int)b->groups.size() - 1;
+            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, &b->groups[gi].cfg)) {
+                batch_free(b);
+                return OPO_E_UNSUPPORTED;
+            }
+        }
+        b->groups[gi].ctxs.push_back(c);
+    }
+    int rc = OPO_OK;
+    b->ev.assign(count, nullptr);
+    for (int i = 0; i < count && rc == OPO_OK; i++)
+        rc = cuda_status(cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming));
+    if (rc == OPO_OK)
+        rc = cuda_status(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    if (b->groups.size() > 1) {
+        for (BatchGroup &gg : b->groups) {
+            if (rc != OPO_OK)
+                break;
+            rc = cuda_status(cudaStreamCreateWithFlags(&gg.stream, cudaStreamNonBlocking));
+            if (rc == OPO_OK)
+                rc = cuda_status(cudaEventCreateWithFlags(&gg.done, cudaEventDisableTiming));
+        }
+    }
+    if (rc != OPO_OK) {
+        batch_free(b);
+        return rc;
+    }
     *out = b;
     return OPO_OK;
 }
@@ -685,28 +739,50 @@ int opo_batch_run(opo_batch *b, int64_t m)
         return OPO_E_CUDA;
     cudaStream_t s = c0->stream;
     const int count = (int)b->ctxs.size();
+    for (const BatchGroup &gg : b->groups)
+        for (opo_ctx *c : gg.ctxs) {
+            int rc = begin_call(c, m, gg.cfg.cluster, false);
+            if (rc != OPO_OK)
+                return rc;
+        }
     for (int i = 0; i < count; i++) {
         opo_ctx *c = b->ctxs[i];
-        int rc = begin_call(c, m, b->cfg.cluster, false);
-        if (rc != OPO_OK)
-            return rc;
         if (c->stream != s) {
             cudaEventRecord(b->ev[i], c->stream);
             cudaStreamWaitEvent(s, b->ev[i], 0);
         }
     }
-    int rc = m > 0 ? fused_run(b->ctxs.data(), count, b->cfg, m, s) : OPO_OK;
-    for (int i = 0; i < count && rc == OPO_OK; i++) {
+    int rc = OPO_OK;
+    if (m > 0) {
+        if (b->groups.size() == 1) {
+            BatchGroup &gg = b->groups[0];
+            rc = fused_run(gg.ctxs.data(), (int)gg.ctxs.size(), gg.cfg, m, s);
+        } else {
+            cudaEventRecord(b->fork, s);
+            for (BatchGroup &gg : b->groups) {
+                if (rc != OPO_OK)
+                    break;
+                cudaStreamWaitEvent(gg.stream, b->fork, 0);
+                rc = fused_run(gg.ctxs.data(), (int)gg.ctxs.size(), gg.cfg, m, gg.stream);
+                cudaEventRecord(gg.done, gg.stream);
+                cudaStreamWaitEvent(s, gg.done, 0);
+            }
+        }
+    }
+    for (const BatchGroup &gg : b->groups)
+        for (opo_ctx *c : gg.ctxs) {
+            c->rt += m;
+            c->last_M = m;
+            c->last_parts = gg.cfg.cluster;
+            c->last_path = OPO_PATH_FUSED;
+            c->last_cluster = gg.cfg.cluster;
+        }
+    for (int i = 0; i < count; i++) {
         opo_ctx *c = b->ctxs[i];
         if (c->stream != s) {
             cudaEventRecord(b->ev[i], s);
             cudaStreamWaitEvent(c->stream, b->ev[i], 0);
         }
-        c->rt += m;
-        c->last_M = m;
-        c->last_parts = b->cfg.cluster;
-        c->last_path = OPO_PATH_FUSED;
-        c->last_cluster = b->cfg.cluster;
     }
     return rc;
 }
@@ -715,13 +791,9 @@ int opo_batch_destroy(opo_batch *b)
 {
     if (!b)
         return OPO_OK;
-    if (!b->ctxs.empty()) {
-        DeviceGuard g(b->ctxs[0]->device);
-        cudaStreamSynchronize(b->ctxs[0]->stream);
-        for (cudaEvent_t e : b->ev)
-            cudaEventDestroy(e);
-    }
-    delete b;
+    DeviceGuard g(b->ctxs[0]->device);
+    cudaStreamSynchronize(b->ctxs[0]->stream);
+    batch_free(b);
     return OPO_OK;
 }
 

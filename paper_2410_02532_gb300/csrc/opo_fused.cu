@@ -32,8 +32,7 @@
 
 #include <cooperative_groups.h>
 
-#include "opo_common.cuh"
-#include "opo_internal.h"
+#include "opo_fused_desc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -42,71 +41,6 @@ namespace {
 
 constexpr int kMaxCluster = 16;
 constexpr int kFusedThreads = 256;
-
-struct InstDesc {
-    void *fields;      // F*N state (read at start, written at end)
-    void *out;         // F*N output-coupled fields of the last round trip
-    const void *pump;  // N input pump
-    const void *disp;  // F*N dispersion factors / N (natural order)
-    const void *gdd;   // F*N cavity spectral factors / N (natural order)
-    const void *tw;    // N twiddles W_N^j
-    const void *ekz;   // 4 nz + 1 factors e^{i dk q dz/4}
-    double *obs;       // raw sums of slot 0 of this call: [slot][C][kNslot]
-    double *trace;     // rows {P_p, P_s, P_i, nu_c} of this call
-    int *err;          // sticky error word
-    int n, logn, logP, logQ, F, nz;
-    unsigned resmask;
-    int use_dk, eom;
-    double kappa[3], h;
-    double bc_re[3], bc_im[3], outscale[3];
-    double eom_beta, eom_f, t_rt, dt, t_window;
-    double pscale[3];  // n eps0 c / 2 * pi w0^2
-    int64_t m_start;   // round-trip counter at the start of the call
-};
-
-// Observables of every instance and slot of the call: output power
-// (1/N) Sum|A|^2 (1 - R) n eps0 c/2 pi w0^2 and the signal centroid
-// Sum k'|X_k|^2 / Sum |X_k|^2 / T, reduced over the C partial sums in a fixed
-// order.
-__global__ void k_finalize_fused(const InstDesc *__restrict__ descs, int count, int C, int M)
-{
-    const int64_t total = (int64_t)count * M;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(t / M), s = (int)(t % M);
-        const InstDesc &d = descs[i];
-        double sum[kNslot] = {0, 0, 0, 0, 0};
-        for (int c = 0; c < C; c++)
-            for (int q = 0; q < kNslot; q++)
-                sum[q] += d.obs[((int64_t)s * C + c) * kNslot + q];
-        const double inv_n = 1.0 / (double)d.n;
-        for (int x = 0; x < 3; x++)
-            d.trace[(int64_t)s * 4 + x] =
-                (x < d.F) ? sum[x] * inv_n * d.outscale[x] * d.outscale[x] * d.pscale[x] : 0.0;
-        d.trace[(int64_t)s * 4 + 3] = sum[3] > 0.0 ? (sum[4] / sum[3]) / d.t_window : 0.0;
-    }
-}
-
-__device__ __forceinline__ void block_reduce5(double *v, double *red)
-{
-    for (int q = 0; q < kNslot; q++)
-        for (int o = 16; o > 0; o >>= 1)
-            v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0)
-        for (int q = 0; q < kNslot; q++)
-            red[w * kNslot + q] = v[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < kNslot; q++) {
-            double t = 0.0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); i++)
-                t += red[i * kNslot + q];
-            v[q] = t;
-        }
-    }
-}
 
 template <class T>
 __global__ void __launch_bounds__(kFusedThreads, 1)
@@ -449,10 +383,23 @@ bool cluster_launchable(bool dbl, int C, size_t sm)
 
 } // namespace
 
-bool fused_config(size_t csz, int fmax, int nmin, int nmax, int cluster_req, int rtpl_req,
-                  FusedCfg *out)
+bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluster_req,
+                  int rtpl_req, FusedCfg *out)
 {
+    const bool dbl = csz == sizeof(double2);
     const int lognmin = ilog2((unsigned)nmin), lognmax = ilog2((unsigned)nmax);
+    // one size and one field count: the size-specialised kernel if it holds it
+    if (nmin == nmax && fmin == fmax) {
+        const int order[5] = {8, 16, 4, 2, 1}; // default cluster sizes, best first
+        for (int i = 0; i < 5; i++) {
+            if (cluster_req > 0 && order[i] != cluster_req)
+                continue;
+            if (fused2_config(dbl, fmax, lognmax, order[i], out)) {
+                out->rt_per_launch = rtpl_req > 0 ? rtpl_req : 64;
+                return true;
+            }
+        }
+    }
     const int logPmin = lognmin / 2;
     const int lmax = 1 << (lognmax - lognmax / 2); // Q >= P, so the largest sub-length is Q
     // Default: the smallest cluster that keeps at most kTargetNc points per
@@ -472,8 +419,9 @@ bool fused_config(size_t csz, int fmax, int nmin, int nmax, int cluster_req, int
             const size_t sm = smem_bytes(csz, fmax, nc, lmax, ds == 1);
             if (sm > kSmemLimit)
                 continue;
-            if (!cluster_launchable(csz == sizeof(double2), C, sm))
+            if (!cluster_launchable(dbl, C, sm))
                 break;
+            best.kernel = 1;
             best.cluster = C;
             best.threads = kFusedThreads;
             best.rt_per_launch = rtpl_req > 0 ? rtpl_req : 64;
@@ -490,9 +438,48 @@ bool fused_config(size_t csz, int fmax, int nmin, int nmax, int cluster_req, int
     return found;
 }
 
-int fused_max_active(bool dbl, int cluster, size_t smem)
+int fused_max_active(bool dbl, int F, int n, const FusedCfg &cfg)
 {
-    return dbl ? max_active<double>(cluster, smem) : max_active<float>(cluster, smem);
+    if (cfg.kernel == 2)
+        return fused2_max_active(dbl, F, ilog2((unsigned)n), cfg);
+    return dbl ? max_active<double>(cfg.cluster, cfg.smem) : max_active<float>(cfg.cluster, cfg.smem);
+}
+
+void fill_desc(InstDesc &d, const opo_ctx *c)
+{
+    d.fields = c->d_fields;
+    d.out = c->d_out;
+    d.pump = c->d_pump;
+    d.disp = c->d_disp;
+    d.gdd = c->d_gdd;
+    d.tw = c->d_tw;
+    d.ekz = c->d_ekz;
+    d.obs = c->d_obs;
+    d.trace = c->d_trace;
+    d.err = (int *)((char *)c->d_ctl + offsetof(DevCtl, err));
+    d.n = c->n;
+    d.logn = c->logn;
+    d.logP = c->logn / 2;
+    d.logQ = c->logn - d.logP;
+    d.F = c->F;
+    d.nz = c->crystal.nz;
+    d.resmask = c->cavity.resonant_mask;
+    d.use_dk = c->dv.use_dk;
+    d.eom = c->dv.eom;
+    for (int x = 0; x < 3; x++) {
+        d.kappa[x] = c->dv.kappa[x];
+        d.bc_re[x] = c->dv.bc_re[x];
+        d.bc_im[x] = c->dv.bc_im[x];
+        d.outscale[x] = c->dv.outscale[x];
+        d.pscale[x] = c->dv.pscale[x];
+    }
+    d.h = c->dv.h;
+    d.eom_beta = c->cavity.eom_beta_rad;
+    d.eom_f = c->cavity.eom_f_hz;
+    d.t_rt = c->cavity.t_rt_s > 0.0 ? c->cavity.t_rt_s : c->grid.t_window_s;
+    d.dt = c->grid.t_window_s / (double)c->n;
+    d.t_window = c->grid.t_window_s;
+    d.m_start = c->rt;
 }
 
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s)
@@ -502,61 +489,28 @@ int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, c
     int fmax = 0, nc_max = 0, lmax = 0;
     std::vector<InstDesc> h(count);
     for (int i = 0; i < count; i++) {
-        const opo_ctx *c = ctxs[i];
-        InstDesc &d = h[i];
-        d.fields = c->d_fields;
-        d.out = c->d_out;
-        d.pump = c->d_pump;
-        d.disp = c->d_disp;
-        d.gdd = c->d_gdd;
-        d.tw = c->d_tw;
-        d.ekz = c->d_ekz;
-        d.obs = c->d_obs;
-        d.trace = c->d_trace;
-        d.err = (int *)((char *)c->d_ctl + offsetof(DevCtl, err));
-        d.n = c->n;
-        d.logn = c->logn;
-        d.logP = c->logn / 2;
-        d.logQ = c->logn - d.logP;
-        d.F = c->F;
-        d.nz = c->crystal.nz;
-        d.resmask = c->cavity.resonant_mask;
-        d.use_dk = c->dv.use_dk;
-        d.eom = c->dv.eom;
-        for (int x = 0; x < 3; x++) {
-            d.kappa[x] = c->dv.kappa[x];
-            d.bc_re[x] = c->dv.bc_re[x];
-            d.bc_im[x] = c->dv.bc_im[x];
-            d.outscale[x] = c->dv.outscale[x];
-        }
-        d.h = c->dv.h;
-        d.eom_beta = c->cavity.eom_beta_rad;
-        d.eom_f = c->cavity.eom_f_hz;
-        d.t_rt = c->cavity.t_rt_s > 0.0 ? c->cavity.t_rt_s : c->grid.t_window_s;
-        d.dt = c->grid.t_window_s / (double)c->n;
-        d.t_window = c->grid.t_window_s;
-        for (int x = 0; x < 3; x++)
-            d.pscale[x] = c->dv.pscale[x];
-        d.m_start = c->rt;
-        fmax = std::max(fmax, c->F);
-        nc_max = std::max(nc_max, c->n / cfg.cluster);
-        lmax = std::max(lmax, 1 << std::max(d.logP, d.logQ));
+        fill_desc(h[i], ctxs[i]);
+        fmax = std::max(fmax, ctxs[i]->F);
+        nc_max = std::max(nc_max, ctxs[i]->n / cfg.cluster);
+        lmax = std::max(lmax, 1 << std::max(h[i].logP, h[i].logQ));
     }
     // descriptors: a device copy owned by this call, freed stream-ordered
     InstDesc *dd = nullptr;
     if (cudaMallocAsync((void **)&dd, sizeof(InstDesc) * count, s) != cudaSuccess)
         return OPO_E_NOMEM;
+    // the pageable source is staged before cudaMemcpyAsync returns
     if (cudaMemcpyAsync(dd, h.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return OPO_E_CUDA;
-    // the pageable source above is consumed before cudaMemcpyAsync returns
-    const size_t sm = smem_bytes(c0->csz, fmax, nc_max, lmax, cfg.disp_in_smem);
-    if (dbl) {
-        cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    } else {
-        cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const size_t sm = cfg.kernel == 2 ? cfg.smem : smem_bytes(c0->csz, fmax, nc_max, lmax, cfg.disp_in_smem);
+    if (cfg.kernel == 1) {
+        if (dbl) {
+            cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        } else {
+            cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(k_fused<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        }
     }
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(count * cfg.cluster);
@@ -574,14 +528,17 @@ int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, c
     for (int64_t done = 0; done < m && rc == OPO_OK; done += cfg.rt_per_launch) {
         int chunk = (int)std::min<int64_t>(cfg.rt_per_launch, m - done);
         int last = (done + chunk >= m) ? 1 : 0;
+        if (cfg.kernel == 2) {
+            rc = fused2_launch(dbl, c0->F, c0->logn, dd, count, cfg, (int)done, chunk, last, s);
+            continue;
+        }
         cudaError_t e;
-        if (dbl) {
+        if (dbl)
             e = cudaLaunchKernelEx(&lc, k_fused<double>, (const InstDesc *)dd, (int)done, chunk, last,
                                    (int)cfg.disp_in_smem, fmax, nc_max, lmax);
-        } else {
+        else
             e = cudaLaunchKernelEx(&lc, k_fused<float>, (const InstDesc *)dd, (int)done, chunk, last,
                                    (int)cfg.disp_in_smem, fmax, nc_max, lmax);
-        }
         if (e != cudaSuccess)
             rc = OPO_E_CUDA;
     }

@@ -1,0 +1,68 @@
+// opo_fused2.cu -- configuration and dispatch of the size-specialised fused
+// kernel (opo_fused2.cuh); the kernels are instantiated in opo_fused2_*.cu.
+#include <algorithm>
+
+#include "opo_fused2.cuh"
+
+namespace opo {
+namespace {
+
+int dispatch(int op, bool dbl, int F, int logn, const InstDesc *dd, int count, int C, int threads,
+             size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
+{
+    if (dbl)
+        return F == 3 ? f2::dispatch_f64_f3(op, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s)
+                      : f2::dispatch_f64_f2(op, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
+    return F == 3 ? f2::dispatch_f32_f3(op, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s)
+                  : f2::dispatch_f32_f2(op, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
+}
+
+} // namespace
+
+bool fused2_config(bool dbl, int F, int logn, int C, FusedCfg *out)
+{
+    if (logn < 12 || logn > 15)
+        return false;
+    const int LP = logn / 2, LQ = logn - LP;
+    if ((1 << LP) < C || (1 << LQ) < C)
+        return false;
+    const int A1 = LP - (LP + 1) / 2;
+    const int B1 = LQ - (LQ + 1) / 2, B2 = (LQ + 1) / 2;
+    const int nc = (1 << logn) / C;
+    const int Qc = (1 << LQ) / C, Pc = (1 << LP) / C;
+    const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
+    const int LS = (logn + 1) / 2;
+    const int maxT = dbl ? 256 : 384;
+    int items = std::max({F * Qc * (1 << A1), F * Pc * (1 << B2), F * Pc * (1 << B1)});
+    int threads = std::min(maxT, ((items + 31) / 32) * 32);
+    for (int ds = 1; ds >= 0; ds--) {
+        size_t el = (size_t)F * nc * (ds ? 4 : 3) + (1 << LQ) + (1 << LS) + ((1 << logn) >> LS);
+        size_t sm = el * csz + 32 * kNslot * sizeof(double);
+        if (sm > 227 * 1024)
+            continue;
+        if (dispatch(1, dbl, F, logn, nullptr, 0, C, threads, sm, ds == 1, 0, 0, 0, nullptr) < 1)
+            continue;
+        out->cluster = C;
+        out->threads = threads;
+        out->disp_in_smem = ds == 1;
+        out->smem = sm;
+        out->kernel = 2;
+        return true;
+    }
+    return false;
+}
+
+int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg)
+{
+    return dispatch(1, dbl, F, logn, nullptr, 0, cfg.cluster, cfg.threads, cfg.smem,
+                    cfg.disp_in_smem, 0, 0, 0, nullptr);
+}
+
+int fused2_launch(bool dbl, int F, int logn, const InstDesc *dd, int count, const FusedCfg &cfg,
+                  int r_base, int chunk, int last, cudaStream_t s)
+{
+    return dispatch(0, dbl, F, logn, dd, count, cfg.cluster, cfg.threads, cfg.smem,
+                    cfg.disp_in_smem, r_base, chunk, last, s);
+}
+
+} // namespace opo

@@ -1,0 +1,546 @@
+#pragma once
+// opo_fused2.cuh -- fused round-trip kernel specialised at compile time for
+// N = P Q with P = 2^LP in {64, 128}, Q = 2^LQ in {64, 128, 256} (N = 2^12 ...
+// 2^15), field count F and precision.  Same method, layout and cluster
+// exchange as the generic fused kernel (opo_fused.cu: time domain columns in
+// X, frequency-domain rows in Y, two cluster barriers per z-step), with every
+// transform split into exactly two Stockham stages whose radices mirror
+// between the forward and inverse transform:
+//   columns  forward [Ra1, Ra2]   inverse [Ra2, Ra1]
+//   rows     forward [Rb1, Rb2]   inverse [Rb2, Rb1]
+// so that the inverse column transform's last stage, the two RK4 half steps
+// that meet at a z-step boundary (Sec. 2.2: N/2 of step j, then N/2 of step
+// j+1) and the next forward column stage all act on the same R values per
+// field in one thread's registers ("block A"), and the forward row
+// transform's last stage, the dispersion factor and the inverse row
+// transform's first stage likewise ("block B").  A z-step is then six
+// shared-memory passes:
+//   A   S -> X   inverse col stage 2, RK4 x2, forward col stage 1
+//   2   X -> Y'  forward col stage 2, W_N^{n2 k1}, push to the owner CTA
+//   --- cluster barrier
+//   3   Y -> S   forward row stage 1
+//   B   S -> Y   forward row stage 2, x D (or G), inverse row stage 1
+//   5   Y -> X'  inverse row stage 2, W_N^{-n2 k1}, push to the owner CTA
+//   --- cluster barrier
+//   6   X -> S   inverse col stage 1
+// Rows are stored with an XOR swizzle of the element index so that the
+// stride-R stores of a first stage do not collide in shared-memory banks.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "opo_fused_desc.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace opo {
+namespace f2 {
+
+template <class T> struct F2Traits;
+template <> struct F2Traits<float> {
+    static constexpr int kMaxThreads = 384;
+    static constexpr int kSwz = 4; // 16 float2 per 128-byte bank row
+};
+template <> struct F2Traits<double> {
+    static constexpr int kMaxThreads = 256;
+    static constexpr int kSwz = 3; // 8 double2 per 128-byte bank row
+};
+
+constexpr int kMaxCl = 16;
+
+template <int R, int DIR, class V>
+__device__ __forceinline__ void dft_r(V *v)
+{
+    dft<R, DIR>(v);
+}
+
+template <class T, int F, int LP, int LQ>
+__global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
+    k_fused2(const InstDesc *__restrict__ descs, int r_base, int M, int write_out, int disp_smem)
+{
+    using V = cv<T>;
+    constexpr int Q = 1 << LQ, LN = LP + LQ, N = 1 << LN;
+    constexpr int A2 = (LP + 1) / 2, A1 = LP - A2; // columns [Ra1, Ra2]
+    constexpr int B2 = (LQ + 1) / 2, B1 = LQ - B2; // rows    [Rb1, Rb2]
+    constexpr int Ra1 = 1 << A1, Ra2 = 1 << A2, Rb1 = 1 << B1, Rb2 = 1 << B2;
+    constexpr int LS = (LN + 1) / 2; // W_N^a = hi[a >> LS] lo[a & (2^LS - 1)]
+    constexpr int SW = F2Traits<T>::kSwz;
+    constexpr int SWM = (1 << SW) - 1;
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int c = (int)cluster.block_rank();
+    const int inst = blockIdx.x / C;
+    const int logC = ilog2((unsigned)C);
+    const int logPc = LP - logC, logQc = LQ - logC;
+    const int Pc = 1 << logPc, Qc = 1 << logQc;
+    const int NC = N >> logC;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *X = reinterpret_cast<V *>(smem_raw);
+    V *Y = X + F * NC;
+    V *S = Y + F * NC;
+    V *Dsm = S + F * NC;
+    V *twQ = Dsm + (disp_smem ? F * NC : 0);
+    V *twLo = twQ + Q;
+    V *twHi = twLo + (1 << LS);
+    double *red = reinterpret_cast<double *>(twHi + (N >> LS));
+    __shared__ V *rX[kMaxCl];
+    __shared__ V *rY[kMaxCl];
+
+    // ---- descriptor scalars into registers
+    const InstDesc &dg = descs[inst];
+    const unsigned resmask = dg.resmask;
+    const int nz = dg.nz;
+    const bool use_e = dg.use_dk != 0;
+    const bool eom = dg.eom != 0;
+    const T kap[3] = {(T)dg.kappa[0], (T)dg.kappa[1], (T)dg.kappa[2]};
+    const T h = (T)dg.h;
+    V bc[3], osc[3];
+    for (int x = 0; x < 3; x++) {
+        bc[x] = cmk<V>((T)dg.bc_re[x], (T)dg.bc_im[x]);
+        osc[x] = cmk<V>((T)dg.outscale[x], (T)0);
+    }
+    const double eom_beta = dg.eom_beta, eom_f = dg.eom_f, t_rt = dg.t_rt, dt = dg.dt;
+    const int64_t m_start = dg.m_start;
+    V *gF = (V *)dg.fields;
+    V *gOut = (V *)dg.out;
+    const V *gPump = (const V *)dg.pump;
+    const V *gD = (const V *)dg.disp;
+    const V *gG = (const V *)dg.gdd;
+    const V *ekz = (const V *)dg.ekz;
+    const V *gtw = (const V *)dg.tw;
+    double *obs = dg.obs;
+    int *err = dg.err;
+
+    for (int i = threadIdx.x; i < Q; i += blockDim.x)
+        twQ[i] = gtw[i << LP];
+    for (int i = threadIdx.x; i < (1 << LS); i += blockDim.x)
+        twLo[i] = gtw[i];
+    for (int i = threadIdx.x; i < (N >> LS); i += blockDim.x)
+        twHi[i] = gtw[i << LS];
+    if (threadIdx.x < C) {
+        rX[threadIdx.x] = cluster.map_shared_rank(X, (unsigned)threadIdx.x);
+        rY[threadIdx.x] = cluster.map_shared_rank(Y, (unsigned)threadIdx.x);
+    }
+    if (disp_smem) {
+        for (int i = threadIdx.x; i < F * NC; i += blockDim.x) {
+            int f = i / NC, p = i - f * NC;
+            int row = p >> LQ, k2 = p & (Q - 1);
+            Dsm[i] = gD[f * N + (c << logPc) + row + (k2 << LP)];
+        }
+    }
+
+    // ---- index helpers
+    auto cidx = [=](int f, int n1, int b) { return f * NC + (n1 << logQc) + b; };
+    auto ridx = [=](int f, int row, int e) {
+        return f * NC + (row << LQ) + (e ^ ((e >> SW) & SWM));
+    };
+    auto gtime = [=](int n1, int b) { return (n1 << LQ) + (c << logQc) + b; };
+    auto twP = [&](int e) { return twQ[e << (LQ - LP)]; }; // W_P^e
+    auto twN = [&](unsigned a) {
+        a &= (unsigned)(N - 1);
+        return cmul(twHi[a >> LS], twLo[a & ((1u << LS) - 1)]);
+    };
+
+    // ---- block A: shared by every z-step boundary
+    // mode 0: first round trip of the launch, input from global memory
+    // mode 1: interior z-step boundary
+    // mode 2: end of the crystal pass (observables, then cavity forward)
+    // mode 3: end of the cavity visit (mirror, EOM, then entry of the next
+    //         round trip, or the final store)
+    auto block_a = [&](auto mode_tag, int qa, int qb, int64_t m_cav, bool next_rt, bool save_out,
+                       double *acc) {
+        constexpr int mode = decltype(mode_tag)::value;
+        const V e0a = use_e ? ekz[qa] : cmk<V>((T)1, (T)0);
+        const V e1a = use_e ? ekz[qa + 1] : e0a;
+        const V e2a = use_e ? ekz[qa + 2] : e0a;
+        const V e0b = use_e ? ekz[qb] : cmk<V>((T)1, (T)0);
+        const V e1b = use_e ? ekz[qb + 1] : e0b;
+        const V e2b = use_e ? ekz[qb + 2] : e0b;
+        for (int u = threadIdx.x; u < (Qc << A2); u += blockDim.x) {
+            const int b = u & (Qc - 1), j = u >> logQc; // j < Ra2
+            V v[F][Ra1];
+            if constexpr (mode == 0) {
+#pragma unroll
+                for (int r = 0; r < Ra1; r++) {
+                    const int g = gtime(j + r * Ra2, b);
+#pragma unroll
+                    for (int f = 0; f < F; f++)
+                        v[f][r] = gF[f * N + g];
+                }
+            } else {
+                // inverse column stage 2: radix Ra1, Ns = Ra2, k = j
+#pragma unroll
+                for (int f = 0; f < F; f++) {
+#pragma unroll
+                    for (int r = 0; r < Ra1; r++)
+                        v[f][r] = S[cidx(f, j + r * Ra2, b)];
+#pragma unroll
+                    for (int r = 1; r < Ra1; r++) {
+                        V w = twP(r * j);
+                        w.y = -w.y;
+                        v[f][r] = cmul(v[f][r], w);
+                    }
+                    dft_r<Ra1, 1>(v[f]);
+                }
+            }
+            // time domain: v[f][r] at n1 = j + r Ra2
+            if constexpr (mode == 1 || mode == 2) {
+#pragma unroll
+                for (int r = 0; r < Ra1; r++) {
+                    V y[F];
+#pragma unroll
+                    for (int f = 0; f < F; f++)
+                        y[f] = v[f][r];
+                    rk4_point<F>(y, e0a, e1a, e2a, kap, h, use_e);
+#pragma unroll
+                    for (int f = 0; f < F; f++)
+                        v[f][r] = y[f];
+                }
+            }
+            if constexpr (mode == 2) {
+#pragma unroll
+                for (int r = 0; r < Ra1; r++) {
+#pragma unroll
+                    for (int f = 0; f < F; f++) {
+                        acc[f] += (double)cabs2(v[f][r]);
+                        if (save_out)
+                            gOut[f * N + gtime(j + r * Ra2, b)] = cmul(v[f][r], osc[f]);
+                    }
+                }
+            }
+            if constexpr (mode == 3) {
+#pragma unroll
+                for (int r = 0; r < Ra1; r++) {
+                    V mod = cmk<V>((T)1, (T)0);
+                    if (eom) {
+                        const int gi = gtime(j + r * Ra2, b);
+                        double uu = eom_f * ((double)(gi - N / 2) * dt) + eom_f * ((double)m_cav * t_rt);
+                        double fr = uu - floor(uu);
+                        T ph;
+                        if constexpr (sizeof(T) == 8)
+                            ph = (T)(eom_beta * sinpi(2.0 * fr));
+                        else
+                            ph = (T)eom_beta * sinpif((T)2 * (T)fr);
+                        T sn, cs;
+                        sincos(ph, &sn, &cs);
+                        mod = cmk<V>(cs, sn);
+                    }
+#pragma unroll
+                    for (int f = 0; f < F; f++) {
+                        if (resmask & (1u << f)) {
+                            V t = cmul(v[f][r], bc[f]);
+                            v[f][r] = eom ? cmul(t, mod) : t;
+                        }
+                    }
+                }
+                if (!next_rt) {
+#pragma unroll
+                    for (int r = 0; r < Ra1; r++)
+#pragma unroll
+                        for (int f = 0; f < F; f++)
+                            gF[f * N + gtime(j + r * Ra2, b)] = v[f][r];
+                    continue;
+                }
+            }
+            if constexpr (mode == 0 || mode == 3) {
+                // entry of a round trip, then its first RK4 half step
+#pragma unroll
+                for (int r = 0; r < Ra1; r++) {
+                    V y[F];
+#pragma unroll
+                    for (int f = 0; f < F; f++) {
+                        y[f] = v[f][r];
+                        if (!(resmask & (1u << f)))
+                            y[f] = (f == 0) ? gPump[gtime(j + r * Ra2, b)] : cmk<V>((T)0, (T)0);
+                    }
+                    rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
+#pragma unroll
+                    for (int f = 0; f < F; f++)
+                        v[f][r] = y[f];
+                }
+            } else if constexpr (mode == 1) {
+#pragma unroll
+                for (int r = 0; r < Ra1; r++) {
+                    V y[F];
+#pragma unroll
+                    for (int f = 0; f < F; f++)
+                        y[f] = v[f][r];
+                    rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
+#pragma unroll
+                    for (int f = 0; f < F; f++)
+                        v[f][r] = y[f];
+                }
+            }
+            // forward column stage 1: radix Ra1, Ns = 1, outputs at j Ra1 + r
+#pragma unroll
+            for (int f = 0; f < F; f++) {
+                dft_r<Ra1, -1>(v[f]);
+#pragma unroll
+                for (int r = 0; r < Ra1; r++)
+                    X[cidx(f, j * Ra1 + r, b)] = v[f][r];
+            }
+        }
+    };
+
+    // ---- phase 2: forward column stage 2 and push into the owners' Y
+    auto phase2 = [&]() {
+        const int items = F * Qc * Ra1;
+        for (int u = threadIdx.x; u < items; u += blockDim.x) {
+            const int b = u & (Qc - 1);
+            const int rest = u >> logQc;
+            const int j = rest & (Ra1 - 1), f = rest >> A1;
+            V v[Ra2];
+#pragma unroll
+            for (int r = 0; r < Ra2; r++)
+                v[r] = X[cidx(f, j + r * Ra1, b)];
+#pragma unroll
+            for (int r = 1; r < Ra2; r++)
+                v[r] = cmul(v[r], twP(r * j));
+            dft_r<Ra2, -1>(v);
+            const int n2 = (c << logQc) + b;
+#pragma unroll
+            for (int r = 0; r < Ra2; r++) {
+                const int k1 = j + r * Ra1;
+                rY[k1 >> logPc][ridx(f, k1 & (Pc - 1), n2)] = cmul(v[r], twN((unsigned)(n2 * k1)));
+            }
+        }
+    };
+
+    // ---- phase 3: forward row stage 1, Y -> S
+    auto phase3 = [&]() {
+        const int items = F * Pc * Rb2;
+        for (int u = threadIdx.x; u < items; u += blockDim.x) {
+            const int j = u & (Rb2 - 1);
+            const int rest = u >> B2;
+            const int row = rest & (Pc - 1), f = rest >> logPc;
+            V v[Rb1];
+#pragma unroll
+            for (int r = 0; r < Rb1; r++)
+                v[r] = Y[ridx(f, row, j + r * Rb2)];
+            dft_r<Rb1, -1>(v);
+#pragma unroll
+            for (int r = 0; r < Rb1; r++)
+                S[ridx(f, row, j * Rb1 + r)] = v[r];
+        }
+    };
+
+    // ---- block B: forward row stage 2, spectral factor, inverse row stage 1
+    auto block_b = [&](bool cav, double *acc) {
+        const int items = F * Pc * Rb1;
+        for (int u = threadIdx.x; u < items; u += blockDim.x) {
+            const int j = u & (Rb1 - 1);
+            const int rest = u >> B1;
+            const int row = rest & (Pc - 1), f = rest >> logPc;
+            V v[Rb2];
+#pragma unroll
+            for (int r = 0; r < Rb2; r++)
+                v[r] = S[ridx(f, row, j + r * Rb1)];
+#pragma unroll
+            for (int r = 1; r < Rb2; r++)
+                v[r] = cmul(v[r], twQ[r * j]);
+            dft_r<Rb2, -1>(v);
+            const int k1 = (c << logPc) + row;
+#pragma unroll
+            for (int r = 0; r < Rb2; r++) {
+                const int k2 = j + r * Rb1;
+                const int k = k1 + (k2 << LP);
+                V fac;
+                if (cav) {
+                    fac = gG[f * N + k];
+                    if (f == 1) {
+                        double p2 = (double)cabs2(v[r]);
+                        acc[3] += p2;
+                        acc[4] += (double)((k < N / 2) ? k : k - N) * p2;
+                    }
+                } else {
+                    fac = disp_smem ? Dsm[f * NC + (row << LQ) + k2] : gD[f * N + k];
+                }
+                v[r] = cmul(v[r], fac);
+            }
+            dft_r<Rb2, 1>(v);
+#pragma unroll
+            for (int r = 0; r < Rb2; r++)
+                Y[ridx(f, row, j * Rb2 + r)] = v[r];
+        }
+    };
+
+    // ---- phase 5: inverse row stage 2 and push into the owners' X
+    auto phase5 = [&]() {
+        const int items = F * Pc * Rb2;
+        for (int u = threadIdx.x; u < items; u += blockDim.x) {
+            const int j = u & (Rb2 - 1);
+            const int rest = u >> B2;
+            const int row = rest & (Pc - 1), f = rest >> logPc;
+            V v[Rb1];
+#pragma unroll
+            for (int r = 0; r < Rb1; r++)
+                v[r] = Y[ridx(f, row, j + r * Rb2)];
+#pragma unroll
+            for (int r = 1; r < Rb1; r++) {
+                V w = twQ[r * j];
+                w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+            dft_r<Rb1, 1>(v);
+            const int k1 = (c << logPc) + row;
+#pragma unroll
+            for (int r = 0; r < Rb1; r++) {
+                const int n2 = j + r * Rb2;
+                V w = twN((unsigned)(n2 * k1));
+                w.y = -w.y;
+                rX[n2 >> logQc][cidx(f, k1, n2 & (Qc - 1))] = cmul(v[r], w);
+            }
+        }
+    };
+
+    // ---- phase 6: inverse column stage 1, X -> S
+    auto phase6 = [&]() {
+        const int items = F * Qc * Ra1;
+        for (int u = threadIdx.x; u < items; u += blockDim.x) {
+            const int b = u & (Qc - 1);
+            const int rest = u >> logQc;
+            const int j = rest & (Ra1 - 1), f = rest >> A1;
+            V v[Ra2];
+#pragma unroll
+            for (int r = 0; r < Ra2; r++)
+                v[r] = X[cidx(f, j + r * Ra1, b)];
+            dft_r<Ra2, 1>(v);
+#pragma unroll
+            for (int r = 0; r < Ra2; r++)
+                S[cidx(f, j * Ra2 + r, b)] = v[r];
+        }
+    };
+
+    // forward transform (after block A), frequency visit, inverse up to S
+    auto middle = [&](bool cav, double *acc) {
+        __syncthreads();
+        phase2();
+        cluster.sync();
+        phase3();
+        __syncthreads();
+        block_b(cav, acc);
+        __syncthreads();
+        phase5();
+        cluster.sync();
+        phase6();
+        __syncthreads();
+    };
+
+    using M0 = std::integral_constant<int, 0>;
+    using M1 = std::integral_constant<int, 1>;
+    using M2 = std::integral_constant<int, 2>;
+    using M3 = std::integral_constant<int, 3>;
+    cluster.sync(); // every CTA of the cluster is running; tables loaded
+    double dummy[kNslot] = {0, 0, 0, 0, 0};
+    block_a(M0{}, 0, 0, 0, true, false, dummy);
+    for (int r = 0; r < M; r++) {
+        const int64_t slot = (int64_t)r_base + r;
+        const int64_t m = m_start + slot;
+        for (int jz = 0; jz + 1 < nz; jz++) {
+            middle(false, dummy);
+            block_a(M1{}, 4 * jz + 2, 4 * (jz + 1), 0, true, false, dummy);
+        }
+        middle(false, dummy);
+        double acc[kNslot] = {0, 0, 0, 0, 0};
+        block_a(M2{}, 4 * (nz - 1) + 2, 0, 0, true, write_out && r == M - 1, acc);
+        middle(true, acc);
+        block_reduce5(acc, red);
+        if (threadIdx.x == 0) {
+            double *o = obs + (slot * C + c) * kNslot;
+            for (int q = 0; q < kNslot; q++)
+                o[q] = acc[q];
+            if (!isfinite(acc[0] + acc[1] + acc[2]))
+                atomicOr(err, 1);
+        }
+        block_a(M3{}, 0, 0, m, r + 1 < M, false, dummy);
+    }
+}
+
+template <class T, int F, int LP, int LQ>
+int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool disp_smem,
+             int r_base, int chunk, int last, cudaStream_t s)
+{
+    auto kern = k_fused2<T, F, LP, LQ>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(count * C);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = sm;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&lc, kern, dd, r_base, chunk, last, (int)disp_smem);
+    return e == cudaSuccess ? OPO_OK : OPO_E_CUDA;
+}
+
+template <class T, int F, int LP, int LQ>
+int max_active_t(int C, int threads, size_t sm)
+{
+    auto kern = k_fused2<T, F, LP, LQ>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(C);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = sm;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &lc) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nclusters;
+}
+
+// Launch (op 0) or occupancy query (op 1) of every instantiated size for one
+// precision and field count; defined by the opo_fused2_*.cu units.
+#define OPO_F2_DISPATCH_DECL(NAME)                                                               \
+    int NAME(int op, int logn, const InstDesc *dd, int count, int C, int threads, size_t sm,    \
+             bool ds, int r_base, int chunk, int last, cudaStream_t s)
+OPO_F2_DISPATCH_DECL(dispatch_f32_f3);
+OPO_F2_DISPATCH_DECL(dispatch_f32_f2);
+OPO_F2_DISPATCH_DECL(dispatch_f64_f3);
+OPO_F2_DISPATCH_DECL(dispatch_f64_f2);
+
+#define OPO_F2_DISPATCH_DEF(NAME, T, F)                                                          \
+    OPO_F2_DISPATCH_DECL(NAME)                                                                   \
+    {                                                                                            \
+        switch (logn) {                                                                          \
+        case 12:                                                                                 \
+            return op == 0 ? launch_t<T, F, 6, 6>(dd, count, C, threads, sm, ds, r_base, chunk,  \
+                                                  last, s)                                       \
+                           : max_active_t<T, F, 6, 6>(C, threads, sm);                           \
+        case 13:                                                                                 \
+            return op == 0 ? launch_t<T, F, 6, 7>(dd, count, C, threads, sm, ds, r_base, chunk,  \
+                                                  last, s)                                       \
+                           : max_active_t<T, F, 6, 7>(C, threads, sm);                           \
+        case 14:                                                                                 \
+            return op == 0 ? launch_t<T, F, 7, 7>(dd, count, C, threads, sm, ds, r_base, chunk,  \
+                                                  last, s)                                       \
+                           : max_active_t<T, F, 7, 7>(C, threads, sm);                           \
+        case 15:                                                                                 \
+            return op == 0 ? launch_t<T, F, 7, 8>(dd, count, C, threads, sm, ds, r_base, chunk,  \
+                                                  last, s)                                       \
+                           : max_active_t<T, F, 7, 8>(C, threads, sm);                           \
+        default:                                                                                 \
+            return op == 0 ? OPO_E_UNSUPPORTED : 0;                                              \
+        }                                                                                        \
+    }
+
+} // namespace f2
+} // namespace opo

@@ -1,0 +1,8 @@
+// Instantiates the size-specialised fused kernel for double fields, 3 fields.
+#include "opo_fused2.cuh"
+
+namespace opo {
+namespace f2 {
+OPO_F2_DISPATCH_DEF(dispatch_f64_f3, double, 3)
+} // namespace f2
+} // namespace opo

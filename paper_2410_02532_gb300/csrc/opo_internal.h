@@ -36,6 +36,7 @@ struct Derived {
 };
 
 struct FusedCfg {
+    int kernel = 1;      // 1: generic fused kernel, 2: size-specialised kernel
     int cluster;         // CTAs per instance
     int threads;         // threads per CTA
     int rt_per_launch;   // round trips per launch
@@ -105,9 +106,9 @@ int plain_pass_raw(void *fields, void *scratch, const void *tw, const void *disp
 
 // opo_fused.cu: a cluster configuration able to hold instances with up to
 // fmax fields and nmin..nmax points (false if none fits or can launch).
-bool fused_config(size_t csz, int fmax, int nmin, int nmax, int cluster_req, int rtpl_req,
-                  FusedCfg *out);
-int fused_max_active(bool dbl, int cluster, size_t smem);
+bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluster_req,
+                  int rtpl_req, FusedCfg *out);
+int fused_max_active(bool dbl, int F, int n, const FusedCfg &cfg);
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s);
 
 } // namespace opo

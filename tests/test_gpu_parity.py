@@ -276,3 +276,72 @@ def test_full_size_n65536_round_trip():
     ref = oracle_rt(cfg, a0, m0=1)
     got = gpu_rt(cfg, a0, opo.OPO_FP32_PH64, opo.OPO_PATH_AUTO, m0=1)
     compare(cfg, got, ref, opo.OPO_FP32_PH64, "n65536")
+
+
+# --------------------------- size-specialised fused kernel (N = 2^12..2^15)
+
+V2_CASES = {
+    "sro_gdd_4096": (lambda: cfg_dispersive(n=4096, nz=8), 3e6),
+    "sync_eom_delay_8192": (lambda: cfg_sync(n=8192).replace(nz=6), 1e6),
+    "degenerate_dk_4096": (lambda: cfg_degenerate(n=4096).replace(nz=10), 1e6),
+    "dro_loss_dk_16384": (lambda: cfg_dro(n=16384).replace(nz=4), 2e6),
+    "sro_32768": (lambda: cfg_dispersive(n=32768, nz=4), 3e6),
+}
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=["fp64", "fp32ph64"])
+@pytest.mark.parametrize("case", sorted(V2_CASES))
+def test_specialised_fused_round_trip(case, prec):
+    make, amp = V2_CASES[case]
+    cfg = make()
+    a0 = strong(cfg, amp)
+    ref = oracle_rt(cfg, a0, m0=5)
+    try:
+        got = gpu_rt(cfg, a0, prec, opo.OPO_PATH_FUSED, m0=5)
+    except opo.OPOError as e:  # FP64 at 2^15 does not fit a cluster
+        assert e.status == opo.OPO_E_UNSUPPORTED and prec == opo.OPO_FP64
+        return
+    compare(cfg, got, ref, prec, case)
+
+
+def test_specialised_fused_two_round_trips_per_pass():
+    """Two round trips in one launch, each checked from the previous state."""
+    cfg = cfg_sync(n=4096).replace(nz=5)
+    a = strong(cfg, 1e6)
+    with opo.Context(cfg, precision=opo.OPO_FP64, fields=a) as ctx:
+        ctx.set_fields(a, rt_index=2)
+        ctx.set_path(opo.OPO_PATH_FUSED)
+        ctx.run(2)
+        got = ctx.get_fields()
+        tr = ctx.trace(2)
+    r1, _, t1 = oracle_rt(cfg, a, m0=2)
+    r2, o2, t2 = oracle_rt(cfg, r1, m0=3)
+    for x in range(cfg.nfields):
+        assert rel_l2(got[x], r2[x]) <= 1e-10
+    assert abs(tr[0, 1] - t1[0, 1]) <= 1e-9 * t1[0, 1]
+    assert abs(tr[1, 1] - t2[0, 1]) <= 1e-9 * t2[0, 1]
+
+
+def test_specialised_batch_and_resume_bitwise():
+    base = cfg_dispersive(n=4096, nz=6)
+    cfgs = [base, base.replace(pump_power=2 * base.pump_power, delay=20e-15),
+            cfg_dro(n=4096).replace(nz=6)]
+    starts = [strong(c, 2e6, i) for i, c in enumerate(cfgs)]
+    alone = []
+    for c, a in zip(cfgs, starts):
+        with opo.Context(c, fields=a) as ctx:
+            ctx.set_path(opo.OPO_PATH_FUSED, 8, 2)
+            ctx.run(3)
+            alone.append((ctx.get_fields(), ctx.trace(3)))
+    ctxs = [opo.Context(c, fields=a) for c, a in zip(cfgs, starts)]
+    try:
+        b = opo.opo_batch_create([c.h for c in ctxs], 8)
+        opo.opo_batch_run(b, 1)
+        opo.opo_batch_run(b, 2)
+        for ctx, (f, t) in zip(ctxs, alone):
+            assert np.array_equal(ctx.get_fields(), f)
+            assert np.array_equal(ctx.trace(2), t[1:])
+        opo.opo_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            c.close()
