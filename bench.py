@@ -47,10 +47,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=0, help="instances per GPU (0: fill the GPU)")
     ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: default)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the headline number (no plain/e2e/cpu legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune", action="store_true", help="default launch shape, no autotuning")
     return ap.parse_args()
 
 
@@ -205,6 +207,7 @@ def main():
     import numpy as np
     import torch
     from paper_2410_02532_gb300 import opo
+    from paper_2410_02532_gb300 import shard
     from paper_2410_02532_gb300 import workloads as W
 
     torch.cuda.set_device(local)
@@ -220,11 +223,18 @@ def main():
         c = base.replace(instance=rank * 100000 + i)
         return opo.Context(c, precision=prec, device=local, stream=s.cuda_stream if s else None)
 
+    tuned = None
+    if not args.no_tune and args.cluster == 0 and args.threads == 0:
+        from paper_2410_02532_gb300 import autotune
+        tuned = autotune.tune(base.replace(instance=rank * 100000 + 50000), prec, device=local)
+    cl_req = tuned["cluster"] if tuned else args.cluster
+    th_req = tuned["threads"] if tuned else args.threads
     probe = make(0)
-    active, cluster = opo.opo_fused_capacity(probe.h, args.cluster)
+    active, cluster = opo.opo_fused_capacity(probe.h, cl_req, th_req)
     B = args.batch if args.batch > 0 else max(1, active)
+    # weak scaling: every rank owns its own block of B instances (seeds differ)
     ctxs = [probe] + [make(i) for i in range(1, B)]
-    batch = opo.opo_batch_create([c.h for c in ctxs], cluster)
+    batch = opo.opo_batch_create([c.h for c in ctxs], cluster, th_req)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -247,12 +257,8 @@ def main():
             evs[k][1].record(stream)
         barrier()
         clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    step_ms = [a.elapsed_time(b_) for a, b_ in evs]
+    total_ms = shard.max_over_ranks(sum(step_ms), dist, device="cuda")
     ms_per_step = total_ms / args.steps
     field_steps = base.nfields * base.nz * B * world
     value = field_steps / (ms_per_step * 1e-3)
@@ -270,8 +276,10 @@ def main():
 
     extras = {}
     if not args.skip_extras and rank == 0:
-        extras = single_and_plain(args, opo, W, base, prec, local, torch)
+        extras = single_and_plain(args, opo, W, base, prec, local, torch, cl_req, th_req)
         extras["e2e"] = e2e(args, opo, W, ctxs, batch, base, torch, np)
+        extras["batched_sweep"] = sweep_leg(opo, W, prec, local, torch)
+        extras["serving"] = serving_leg(prec, local, value, base)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -283,6 +291,7 @@ def main():
                                    % (base.name, B, cluster),
                        "n": base.n, "fields": base.nfields, "nz": base.nz,
                        "instances_per_gpu": B, "cluster": cluster,
+                       "threads_per_cta": th_req, "autotuned": tuned,
                        "precision": "fp32 fields + fp64 phase args" if prec else "fp64",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "instances sharded per GPU, no collective"},
@@ -305,13 +314,16 @@ def main():
     return 0
 
 
-def single_and_plain(args, opo, W, base, prec, local, torch):
+def single_and_plain(args, opo, W, base, prec, local, torch, cl_req=0, th_req=0):
     """One instance alone: fused and plain paths, round trips per second."""
     out = {}
     s = torch.cuda.Stream()
     for name, path in (("single_fused", opo.OPO_PATH_FUSED), ("single_plain", opo.OPO_PATH_PLAIN)):
         ctx = opo.Context(base, precision=prec, device=local, stream=s.cuda_stream)
-        ctx.set_path(path)
+        if path == opo.OPO_PATH_FUSED:
+            ctx.set_path(path, cl_req, 0, th_req)
+        else:
+            ctx.set_path(path)
         steps = max(3, min(args.steps, 10))
         with torch.cuda.stream(s):
             for _ in range(2):
@@ -369,6 +381,61 @@ def e2e(args, opo, W, ctxs, batch, base, torch, np):
             "h2d_bytes_per_step": B * F * n * 16,
             "d2h_bytes_per_step": B * (n * 16 + 32),
             "ms_per_step": dt * 1e3}
+
+
+def sweep_leg(opo, W, prec, local, torch, rounds=2):
+    """The batched sweep: 256 seeded instances (N 2^12..2^15, SRO/DRO/degenerate,
+    1-5x threshold, +-50 fs, 5-30 mm), advanced together; point-field-steps/s."""
+    cfgs = W.sweep_instances(256)
+    s = torch.cuda.Stream()
+    ctxs = [opo.Context(c, precision=prec, device=local, stream=s.cuda_stream) for c in cfgs]
+    try:
+        b = opo.opo_batch_create([c.h for c in ctxs], 0, 0)
+        with torch.cuda.stream(s):
+            opo.opo_batch_run(b, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            opo.opo_batch_run(b, rounds)
+            e1.record(s)
+            e1.synchronize()
+        opo.opo_batch_destroy(b)
+        sec = e0.elapsed_time(e1) * 1e-3
+        pfs = sum(c.n * c.nfields * c.nz for c in cfgs) * rounds
+        fs = sum(c.nfields * c.nz for c in cfgs) * rounds
+        return {"instances": len(cfgs), "round_trips": rounds, "seconds": sec,
+                "point_field_steps_per_s": pfs / sec, "field_steps_per_s": fs / sec,
+                "round_trips_per_s": len(cfgs) * rounds / sec}
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def serving_leg(prec, local, batch_value, base, seconds=12.0):
+    """Poisson request stream through the continuous-batching server at about
+    0.7 of the measured capacity (round-trip budgets scaled to 50..300 so the
+    run takes seconds); p50/p99 latency and throughput."""
+    from paper_2410_02532_gb300 import serving
+    # capacity in point-field-steps/s from the headline batch
+    cap = batch_value * base.n
+    probe = serving.poisson_trace(400, 1.0, rounds=(50, 300))
+    mean_work = sum(serving.request_work(r) for r in probe) / len(probe)
+    rate = 0.7 * cap / mean_work
+    count = max(20, int(rate * seconds))
+    reqs = serving.poisson_trace(count, rate, rounds=(50, 300))
+    srv = serving.Server(precision=prec, device=local, tick_rt=16)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, max_wall_s=4 * seconds)
+    wall = time.perf_counter() - t0
+    st = serving.latency_stats(res)
+    work = sum(serving.request_work(r) for r in reqs if any(x.rid == r.rid for x in res))
+    st.update({"requests": count, "completed": len(res), "rate_hz": rate,
+               "offered_load": 0.7, "rounds_range": [50, 300], "n_range": [4096, 32768],
+               "wall_s": wall, "point_field_steps_per_s": work / wall,
+               "field_steps_per_s": srv.field_steps / wall, "ticks": srv.ticks,
+               "note": "offered load = 0.7 x headline batch capacity (point-field-steps); "
+                       "200 requests/s with 100-5000 round trips (N 2^12..2^15) would offer "
+                       "about %.0fx the capacity" % (200.0 * (2550.0 / 175.0) * 0.7 / rate)})
+    return st
 
 
 if __name__ == "__main__":

@@ -190,19 +190,22 @@ OPO_API int opo_get_fields_device(opo_ctx *ctx, int32_t field, int32_t which, vo
 /* Choose the execution path.  OPO_PATH_PLAIN: one kernel per operation per
  * z-step, replayed as a CUDA graph per round trip.  OPO_PATH_FUSED: one
  * persistent kernel per launch in which a thread-block cluster of `cluster`
- * CTAs keeps the instance's fields in distributed shared memory for
- * `rt_per_launch` round trips.  cluster = 0 / rt_per_launch = 0 pick
- * defaults.  OPO_E_UNSUPPORTED if the fused path cannot hold this instance. */
-OPO_API int opo_set_path(opo_ctx *ctx, int32_t path, int32_t cluster, int32_t rt_per_launch);
+ * CTAs of `threads` threads keeps the instance's fields in distributed shared
+ * memory for `rt_per_launch` round trips.  0 picks the default for each of
+ * cluster, rt_per_launch and threads.  OPO_E_UNSUPPORTED if the fused path
+ * cannot hold the instance in that configuration. */
+OPO_API int opo_set_path(opo_ctx *ctx, int32_t path, int32_t cluster, int32_t rt_per_launch,
+                         int32_t threads);
 
 /* Fused-path capacity on the context's device: how many thread-block
  * clusters of `cluster` CTAs (0: the default size for this instance) with
  * this instance's shared-memory footprint can be resident at once, i.e. how
- * many such instances one batched launch runs concurrently.  *cluster_out
+ * many such instances one batched launch runs concurrently (threads = 0: the
+ * default CTA size).  *cluster_out
  * (optional) receives the cluster size used.  OPO_E_UNSUPPORTED if the fused
  * path cannot hold the instance. */
-OPO_API int opo_fused_capacity(const opo_ctx *ctx, int32_t cluster, int32_t *max_active,
-                               int32_t *cluster_out);
+OPO_API int opo_fused_capacity(const opo_ctx *ctx, int32_t cluster, int32_t threads,
+                               int32_t *max_active, int32_t *cluster_out);
 
 /* Wait for the context's stream; reports a pending device error. */
 OPO_API int opo_sync(opo_ctx *ctx);
@@ -219,11 +222,17 @@ OPO_API const char *opo_status_string(int status);
  * concurrently.  All contexts must be on one device, in one precision, with
  * crystal and cavity set; every other parameter may differ.  The batch keeps
  * pointers to the contexts (owned by the caller; they must outlive the batch)
- * and is ordered on the first context's stream.  Each instance advances
+ * and is ordered on the first context's stream.  opo_batch_run needs every
+ * member alive; opo_batch_destroy does not read the members (it waits for the
+ * device), so a batch may be destroyed after or before its contexts.  Each instance advances
  * bit-for-bit as opo_run_roundtrips would advance it alone on the fused path
- * with the same cluster size (cluster = 0: each group's default).
+ * with the same launch shape: `cluster` and `threads` apply to every
+ * instance when nonzero; where zero, each instance keeps the cluster size,
+ * CTA size and round trips per launch of its own opo_set_path (default 0:
+ * the library's choice for its size class).
  * OPO_E_UNSUPPORTED if some group cannot run with that cluster size. */
-OPO_API int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster);
+OPO_API int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster,
+                             int32_t threads);
 OPO_API int opo_batch_run(opo_batch *batch, int64_t m);
 OPO_API int opo_batch_destroy(opo_batch *batch);
 

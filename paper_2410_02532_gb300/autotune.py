@@ -1,0 +1,117 @@
+"""Autotuner for the fused path: picks the launch shape of an instance class.
+
+An instance class is (N, field count, precision).  Candidates are
+(cluster size, threads per CTA, round trips per launch); each candidate that
+the library accepts is timed on a batch that fills the GPU (as many
+co-resident clusters as the occupancy query allows) with CUDA events on the
+launch stream, and the one with the highest field-steps/s wins.  The choice
+depends only on the class, never on the mix an instance later runs in, so a
+result does not depend on which batch it was computed in.
+
+Results are cached per process and optionally in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import opo
+
+CLUSTERS = (4, 8, 16)
+THREADS = (0, 128, 192, 256, 384)
+RT_PER_LAUNCH = (16, 64)
+
+_cache = {}
+_lock = threading.Lock()
+
+
+def _key(n, nfields, precision):
+    return "%d/%d/%d" % (int(n), int(nfields), int(precision))
+
+
+def load(path):
+    """Merge a JSON cache written by :func:`save`."""
+    if path and os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+        with _lock:
+            _cache.update(data)
+
+
+def save(path):
+    with _lock:
+        data = dict(_cache)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def lookup(n, nfields, precision):
+    with _lock:
+        return _cache.get(_key(n, nfields, precision))
+
+
+def tune(cfg, precision=opo.OPO_FP32_PH64, device=0, round_trips=2, candidates=None):
+    """Time every accepted launch shape for the class of ``cfg``; return the
+    best as ``{"cluster", "threads", "rt_per_launch", "field_steps_per_s"}``.
+
+    ``cfg`` is an ``OPOConfig``; its physics only sets the work per step (all
+    instances of a class cost the same).
+    """
+    import torch
+
+    hit = lookup(cfg.n, cfg.nfields, precision)
+    if hit is not None:
+        return hit
+    stream = torch.cuda.Stream(device=device)
+    results = []
+    cands = candidates or [(c, t, r) for c in CLUSTERS for t in THREADS for r in RT_PER_LAUNCH]
+    probe = opo.Context(cfg, precision=precision, device=device, stream=stream.cuda_stream)
+    try:
+        for (cl, th, rtpl) in cands:
+            try:
+                active, cl_used = opo.opo_fused_capacity(probe.h, cl, th)
+            except opo.OPOError:
+                continue
+            if active < 1:
+                continue
+            ctxs = [probe] + [opo.Context(cfg.replace(instance=cfg.instance + i + 1),
+                                          precision=precision, device=device,
+                                          stream=stream.cuda_stream)
+                              for i in range(active - 1)]
+            try:
+                for c in ctxs:
+                    c.set_path(opo.OPO_PATH_FUSED, cl_used, rtpl, th)
+                batch = opo.opo_batch_create([c.h for c in ctxs], cl_used, th)
+                with torch.cuda.stream(stream):
+                    opo.opo_batch_run(batch, 1)  # warm-up
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    opo.opo_batch_run(batch, round_trips)
+                    e1.record(stream)
+                    e1.synchronize()
+                opo.opo_batch_destroy(batch)
+                sec = e0.elapsed_time(e1) * 1e-3
+                fs = active * cfg.nfields * cfg.nz * round_trips / sec
+                results.append({"cluster": cl_used, "threads": th, "rt_per_launch": rtpl,
+                                "field_steps_per_s": fs, "instances": active})
+            except opo.OPOError:
+                pass
+            finally:
+                for c in ctxs[1:]:
+                    c.close()
+    finally:
+        probe.close()
+    if not results:
+        return None
+    best = max(results, key=lambda r: r["field_steps_per_s"])
+    best = dict(best, candidates=len(results))
+    with _lock:
+        _cache[_key(cfg.n, cfg.nfields, precision)] = best
+    return best
+
+
+__all__ = ["tune", "lookup", "load", "save"]

@@ -240,7 +240,8 @@ int choose_path(opo_ctx *c, FusedCfg *cfg)
 {
     if (c->path_req == OPO_PATH_PLAIN)
         return OPO_PATH_PLAIN;
-    bool ok = fused_config(c->csz, c->F, c->F, c->n, c->n, c->cluster_req, c->rtpl_req, cfg);
+    bool ok = fused_config(c->csz, c->F, c->F, c->n, c->n, c->cluster_req, c->rtpl_req,
+                           c->threads_req, cfg);
     if (c->path_req == OPO_PATH_FUSED)
         return ok ? OPO_PATH_FUSED : -1;
     return ok ? OPO_PATH_FUSED : OPO_PATH_PLAIN;
@@ -506,20 +507,24 @@ int opo_get_fields_device(opo_ctx *c, int32_t field, int32_t which, void *dev, s
     return get_fields_impl(c, field, which, dev, n, true);
 }
 
-int opo_set_path(opo_ctx *c, int32_t path, int32_t cluster, int32_t rt_per_launch)
+int opo_set_path(opo_ctx *c, int32_t path, int32_t cluster, int32_t rt_per_launch,
+                 int32_t threads)
 {
     if (!c || path < OPO_PATH_AUTO || path > OPO_PATH_FUSED)
         return OPO_E_INVALID;
-    if (cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)) || rt_per_launch < 0)
+    if (cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)) || rt_per_launch < 0 ||
+        threads < 0 || threads > 1024 || (threads & 31))
         return OPO_E_INVALID;
     if (path == OPO_PATH_FUSED) {
         FusedCfg cfg;
-        if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, rt_per_launch, &cfg))
+        DeviceGuard g(c->device);
+        if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, rt_per_launch, threads, &cfg))
             return OPO_E_UNSUPPORTED;
     }
     c->path_req = path;
     c->cluster_req = cluster;
     c->rtpl_req = rt_per_launch;
+    c->threads_req = threads;
     return OPO_OK;
 }
 
@@ -599,16 +604,17 @@ int opo_get_trace(opo_ctx *c, double *out, int64_t rows)
     return rc;
 }
 
-int opo_fused_capacity(const opo_ctx *c, int32_t cluster, int32_t *max_active,
+int opo_fused_capacity(const opo_ctx *c, int32_t cluster, int32_t threads, int32_t *max_active,
                        int32_t *cluster_out)
 {
-    if (!c || !max_active || cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)))
+    if (!c || !max_active || cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)) ||
+        threads < 0 || (threads & 31))
         return OPO_E_INVALID;
     DeviceGuard g(c->device);
     if (!g.ok)
         return OPO_E_CUDA;
     FusedCfg cfg;
-    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, &cfg))
+    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, threads, &cfg))
         return OPO_E_UNSUPPORTED;
     *max_active = fused_max_active(c->prec == OPO_FP64, c->F, c->n, cfg);
     if (cluster_out)
@@ -642,6 +648,8 @@ struct opo_batch {
     std::vector<BatchGroup> groups;
     std::vector<cudaEvent_t> ev; // one per context: stream ordering
     cudaEvent_t fork = nullptr;
+    int device = 0;              // copies, so that destroying the batch never
+    cudaStream_t stream = nullptr; // reads a member context
 };
 
 static void batch_free(opo_batch *b)
@@ -662,14 +670,16 @@ static void batch_free(opo_batch *b)
 
 extern "C" {
 
-int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster)
+int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster,
+                     int32_t threads)
 {
     if (!out)
         return OPO_E_INVALID;
     *out = nullptr;
     if (!ctxs || count < 1)
         return OPO_E_INVALID;
-    if (cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)))
+    if (cluster < 0 || cluster > 16 || (cluster > 0 && !is_pow2(cluster)) || threads < 0 ||
+        (threads & 31))
         return OPO_E_INVALID;
     for (int i = 0; i < count; i++) {
         const opo_ctx *c = ctxs[i];
@@ -690,16 +700,31 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
     if (!b)
         return OPO_E_NOMEM;
     b->ctxs.assign(ctxs, ctxs + count);
+    b->device = ctxs[0]->device;
+    b->stream = ctxs[0]->stream;
+    // launch shape of a context: the batch's arguments where nonzero, else the
+    // context's own opo_set_path request
+    auto want = [&](const opo_ctx *c, int *cl, int *th, int *rt) {
+        *cl = cluster > 0 ? cluster : c->cluster_req;
+        *th = threads > 0 ? threads : c->threads_req;
+        *rt = c->rtpl_req;
+    };
     for (int i = 0; i < count; i++) {
         opo_ctx *c = ctxs[i];
+        int cl, th, rt;
+        want(c, &cl, &th, &rt);
         int gi = -1;
-        for (size_t k = 0; k < b->groups.size(); k++)
-            if (b->groups[k].ctxs[0]->n == c->n && b->groups[k].ctxs[0]->F == c->F)
+        for (size_t k = 0; k < b->groups.size(); k++) {
+            const opo_ctx *g0 = b->groups[k].ctxs[0];
+            int cl0, th0, rt0;
+            want(g0, &cl0, &th0, &rt0);
+            if (g0->n == c->n && g0->F == c->F && cl0 == cl && th0 == th && rt0 == rt)
                 gi = (int)k;
+        }
         if (gi < 0) {
             b->groups.emplace_back();
             gi = (int)b->groups.size() - 1;
-            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, &b->groups[gi].cfg)) {
+            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, &b->groups[gi].cfg)) {
                 batch_free(b);
                 return OPO_E_UNSUPPORTED;
             }
@@ -791,8 +816,9 @@ int opo_batch_destroy(opo_batch *b)
 {
     if (!b)
         return OPO_OK;
-    DeviceGuard g(b->ctxs[0]->device);
-    cudaStreamSynchronize(b->ctxs[0]->stream);
+    DeviceGuard g(b->device);
+    // the batch's events may still be pending on the device
+    cudaDeviceSynchronize();
     batch_free(b);
     return OPO_OK;
 }

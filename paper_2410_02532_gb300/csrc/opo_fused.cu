@@ -384,7 +384,7 @@ bool cluster_launchable(bool dbl, int C, size_t sm)
 } // namespace
 
 bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluster_req,
-                  int rtpl_req, FusedCfg *out)
+                  int rtpl_req, int threads_req, FusedCfg *out)
 {
     const bool dbl = csz == sizeof(double2);
     const int lognmin = ilog2((unsigned)nmin), lognmax = ilog2((unsigned)nmax);
@@ -394,12 +394,14 @@ bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluste
         for (int i = 0; i < 5; i++) {
             if (cluster_req > 0 && order[i] != cluster_req)
                 continue;
-            if (fused2_config(dbl, fmax, lognmax, order[i], out)) {
+            if (fused2_config(dbl, fmax, lognmax, order[i], threads_req, out)) {
                 out->rt_per_launch = rtpl_req > 0 ? rtpl_req : 64;
                 return true;
             }
         }
     }
+    if (threads_req > 0 && threads_req != kFusedThreads)
+        return false; // the generic kernel runs kFusedThreads threads
     const int logPmin = lognmin / 2;
     const int lmax = 1 << (lognmax - lognmax / 2); // Q >= P, so the largest sub-length is Q
     // Default: the smallest cluster that keeps at most kTargetNc points per

@@ -19,7 +19,7 @@ int dispatch(int op, bool dbl, int F, int logn, const InstDesc *dd, int count, i
 
 } // namespace
 
-bool fused2_config(bool dbl, int F, int logn, int C, FusedCfg *out)
+bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
     if (logn < 12 || logn > 15)
         return false;
@@ -33,8 +33,15 @@ bool fused2_config(bool dbl, int F, int logn, int C, FusedCfg *out)
     const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
     const int LS = (logn + 1) / 2;
     const int maxT = dbl ? 256 : 384;
-    int items = std::max({F * Qc * (1 << A1), F * Pc * (1 << B2), F * Pc * (1 << B1)});
-    int threads = std::min(maxT, ((items + 31) / 32) * 32);
+    // default: one work item per thread in the column phases (2 and 6);
+    // the row phases may take two rounds
+    int items = F * Qc * (1 << A1);
+    int threads = threads_req > 0 ? threads_req : std::min(maxT, ((items + 31) / 32) * 32);
+    if (threads > maxT || threads < 32 || (threads & 31))
+        return false;
+    (void)B1;
+    (void)B2;
+    (void)Pc;
     for (int ds = 1; ds >= 0; ds--) {
         size_t el = (size_t)F * nc * (ds ? 4 : 3) + (1 << LQ) + (1 << LS) + ((1 << logn) >> LS);
         size_t sm = el * csz + 32 * kNslot * sizeof(double);

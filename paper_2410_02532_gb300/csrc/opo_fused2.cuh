@@ -134,8 +134,11 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
 
     // ---- index helpers
     auto cidx = [=](int f, int n1, int b) { return f * NC + (n1 << logQc) + b; };
+    // rows: the element index is XOR-swizzled within 2^SW-element groups by
+    // its group number and by the row, so that both unit-stride and stride-R
+    // accesses of one or two rows per wavefront hit distinct banks
     auto ridx = [=](int f, int row, int e) {
-        return f * NC + (row << LQ) + (e ^ ((e >> SW) & SWM));
+        return f * NC + (row << LQ) + (e ^ (((e >> SW) ^ (row << (SW - 1))) & SWM));
     };
     auto gtime = [=](int n1, int b) { return (n1 << LQ) + (c << logQc) + b; };
     auto twP = [&](int e) { return twQ[e << (LQ - LP)]; }; // W_P^e
@@ -301,10 +304,14 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
                 v[r] = cmul(v[r], twP(r * j));
             dft_r<Ra2, -1>(v);
             const int n2 = (c << logQc) + b;
+            // W_N^{n2 k1} for k1 = j + r Ra1: base W_N^{n2 j} times step^r
+            const V step = twN((unsigned)(n2 * Ra1));
+            V w = twN((unsigned)(n2 * j));
 #pragma unroll
             for (int r = 0; r < Ra2; r++) {
                 const int k1 = j + r * Ra1;
-                rY[k1 >> logPc][ridx(f, k1 & (Pc - 1), n2)] = cmul(v[r], twN((unsigned)(n2 * k1)));
+                rY[k1 >> logPc][ridx(f, k1 & (Pc - 1), n2)] = cmul(v[r], w);
+                w = cmul(w, step);
             }
         }
     };
@@ -386,12 +393,16 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
             }
             dft_r<Rb1, 1>(v);
             const int k1 = (c << logPc) + row;
+            // W_N^{-n2 k1} for n2 = j + r Rb2: base W_N^{-k1 j} times step^r
+            V step = twN((unsigned)(k1 * Rb2));
+            step.y = -step.y;
+            V w = twN((unsigned)(k1 * j));
+            w.y = -w.y;
 #pragma unroll
             for (int r = 0; r < Rb1; r++) {
                 const int n2 = j + r * Rb2;
-                V w = twN((unsigned)(n2 * k1));
-                w.y = -w.y;
                 rX[n2 >> logQc][cidx(f, k1, n2 & (Qc - 1))] = cmul(v[r], w);
+                w = cmul(w, step);
             }
         }
     };

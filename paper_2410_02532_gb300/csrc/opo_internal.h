@@ -79,7 +79,7 @@ struct opo_ctx {
     int64_t last_M = 0;        // round trips in the last call
     int last_parts = 1;
     opo::Derived dv{};
-    int path_req = OPO_PATH_AUTO, cluster_req = 0, rtpl_req = 0;
+    int path_req = OPO_PATH_AUTO, cluster_req = 0, rtpl_req = 0, threads_req = 0;
     int last_path = OPO_PATH_PLAIN, last_cluster = 0;
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
@@ -107,7 +107,7 @@ int plain_pass_raw(void *fields, void *scratch, const void *tw, const void *disp
 // opo_fused.cu: a cluster configuration able to hold instances with up to
 // fmax fields and nmin..nmax points (false if none fits or can launch).
 bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluster_req,
-                  int rtpl_req, FusedCfg *out);
+                  int rtpl_req, int threads_req, FusedCfg *out);
 int fused_max_active(bool dbl, int F, int n, const FusedCfg &cfg);
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s);
 

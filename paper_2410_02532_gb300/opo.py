@@ -78,14 +78,15 @@ _SIGS = {
                               ctypes.c_int),
     "opo_get_fields_device": ([_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t],
                               ctypes.c_int),
-    "opo_set_path": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "opo_set_path": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+                     ctypes.c_int),
     "opo_sync": ([_P], ctypes.c_int),
-    "opo_fused_capacity": ([_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+    "opo_fused_capacity": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "opo_destroy": ([_P], ctypes.c_int),
     "opo_status_string": ([ctypes.c_int], ctypes.c_char_p),
-    "opo_batch_create": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32],
-                         ctypes.c_int),
+    "opo_batch_create": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
+                          ctypes.c_int32], ctypes.c_int),
     "opo_batch_run": ([_P, ctypes.c_int64], ctypes.c_int),
     "opo_batch_destroy": ([_P], ctypes.c_int),
 }
@@ -180,15 +181,16 @@ def opo_get_fields_device(ctx, field: int, which: int, dev_ptr: int, n: int):
                                        int(n)), "opo_get_fields_device")
 
 
-def opo_set_path(ctx, path: int, cluster: int = 0, rt_per_launch: int = 0):
-    _check(lib().opo_set_path(ctx, int(path), int(cluster), int(rt_per_launch)), "opo_set_path")
+def opo_set_path(ctx, path: int, cluster: int = 0, rt_per_launch: int = 0, threads: int = 0):
+    _check(lib().opo_set_path(ctx, int(path), int(cluster), int(rt_per_launch), int(threads)),
+           "opo_set_path")
 
 
-def opo_fused_capacity(ctx, cluster: int = 0):
+def opo_fused_capacity(ctx, cluster: int = 0, threads: int = 0):
     """(max co-resident clusters, cluster size) of the fused path."""
     a, c = ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().opo_fused_capacity(ctx, int(cluster), ctypes.byref(a), ctypes.byref(c)),
-           "opo_fused_capacity")
+    _check(lib().opo_fused_capacity(ctx, int(cluster), int(threads), ctypes.byref(a),
+                                    ctypes.byref(c)), "opo_fused_capacity")
     return a.value, c.value
 
 
@@ -200,10 +202,10 @@ def opo_destroy(ctx):
     lib().opo_destroy(ctx)
 
 
-def opo_batch_create(ctxs, cluster: int = 0):
+def opo_batch_create(ctxs, cluster: int = 0, threads: int = 0):
     arr = (_P * len(ctxs))(*[c.value if isinstance(c, _P) else c for c in ctxs])
     h = _P()
-    _check(lib().opo_batch_create(ctypes.byref(h), arr, len(ctxs), int(cluster)),
+    _check(lib().opo_batch_create(ctypes.byref(h), arr, len(ctxs), int(cluster), int(threads)),
            "opo_batch_create")
     return h
 
@@ -291,8 +293,8 @@ class Context:
     def get_fields(self, which=OPO_INTRACAVITY):
         return np.stack([opo_get_fields(self.h, x, which, self.n) for x in range(self.nfields)])
 
-    def set_path(self, path, cluster=0, rt_per_launch=0):
-        opo_set_path(self.h, path, cluster, rt_per_launch)
+    def set_path(self, path, cluster=0, rt_per_launch=0, threads=0):
+        opo_set_path(self.h, path, cluster, rt_per_launch, threads)
 
     def run(self, m, stats=True):
         return opo_run_roundtrips(self.h, m, stats)

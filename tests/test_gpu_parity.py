@@ -345,3 +345,22 @@ def test_specialised_batch_and_resume_bitwise():
     finally:
         for c in ctxs:
             c.close()
+
+
+@pytest.mark.parametrize("cluster,threads", [(8, 256), (16, 192), (16, 384), (4, 384)])
+def test_specialised_fused_launch_shapes(cluster, threads):
+    """The same round trip under other cluster and CTA sizes (the autotuner's
+    search space) stays within tolerance of the oracle."""
+    cfg = cfg_dispersive(n=16384, nz=3)
+    a0 = strong(cfg)
+    ref = oracle_rt(cfg, a0)
+    try:
+        with opo.Context(cfg, precision=opo.OPO_FP32_PH64, fields=a0) as ctx:
+            ctx.set_path(opo.OPO_PATH_FUSED, cluster, 0, threads)
+            s = ctx.run(1)
+            got = (ctx.get_fields(), ctx.get_fields(opo.OPO_OUTPUT), ctx.trace(1), s)
+    except opo.OPOError as e:
+        assert e.status == opo.OPO_E_UNSUPPORTED
+        return
+    compare(cfg, got, ref, opo.OPO_FP32_PH64, "C=%d T=%d" % (cluster, threads))
+    assert got[3].cluster == cluster
