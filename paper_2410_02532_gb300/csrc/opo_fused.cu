@@ -390,8 +390,16 @@ bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluste
     const int lognmin = ilog2((unsigned)nmin), lognmax = ilog2((unsigned)nmax);
     // one size and one field count: the size-specialised kernel if it holds it
     if (nmin == nmax && fmin == fmax) {
-        const int order[5] = {8, 16, 4, 2, 1}; // default cluster sizes, best first
-        for (int i = 0; i < 5; i++) {
+        // default: about kTargetNc points per field in each CTA (the shape the
+        // headline size runs best in), then larger, then smaller clusters
+        int c0 = nmax / kTargetNc;
+        c0 = c0 < 1 ? 1 : (c0 > 16 ? 16 : c0);
+        int order[5], no = 0;
+        for (int c = c0; c <= 16; c *= 2)
+            order[no++] = c;
+        for (int c = c0 / 2; c >= 1; c /= 2)
+            order[no++] = c;
+        for (int i = 0; i < no; i++) {
             if (cluster_req > 0 && order[i] != cluster_req)
                 continue;
             if (fused2_config(dbl, fmax, lognmax, order[i], threads_req, out)) {
@@ -442,7 +450,7 @@ bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluste
 
 int fused_max_active(bool dbl, int F, int n, const FusedCfg &cfg)
 {
-    if (cfg.kernel == 2)
+    if (cfg.kernel >= 2)
         return fused2_max_active(dbl, F, ilog2((unsigned)n), cfg);
     return dbl ? max_active<double>(cfg.cluster, cfg.smem) : max_active<float>(cfg.cluster, cfg.smem);
 }
@@ -504,7 +512,7 @@ int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, c
     if (cudaMemcpyAsync(dd, h.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return OPO_E_CUDA;
-    const size_t sm = cfg.kernel == 2 ? cfg.smem : smem_bytes(c0->csz, fmax, nc_max, lmax, cfg.disp_in_smem);
+    const size_t sm = cfg.kernel >= 2 ? cfg.smem : smem_bytes(c0->csz, fmax, nc_max, lmax, cfg.disp_in_smem);
     if (cfg.kernel == 1) {
         if (dbl) {
             cudaFuncSetAttribute(k_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -530,7 +538,7 @@ int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, c
     for (int64_t done = 0; done < m && rc == OPO_OK; done += cfg.rt_per_launch) {
         int chunk = (int)std::min<int64_t>(cfg.rt_per_launch, m - done);
         int last = (done + chunk >= m) ? 1 : 0;
-        if (cfg.kernel == 2) {
+        if (cfg.kernel >= 2) {
             rc = fused2_launch(dbl, c0->F, c0->logn, dd, count, cfg, (int)done, chunk, last, s);
             continue;
         }

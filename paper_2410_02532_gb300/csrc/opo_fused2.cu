@@ -7,14 +7,48 @@
 namespace opo {
 namespace {
 
-int dispatch(int op, bool dbl, int F, int logn, const InstDesc *dd, int count, int C, int threads,
-             size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
+int dispatch(int op, bool ip, bool dbl, int F, int logn, const InstDesc *dd, int count, int C,
+             int threads, size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
 {
     if (dbl)
-        return F == 3 ? f2::dispatch_f64_f3(op, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s)
-                      : f2::dispatch_f64_f2(op, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
-    return F == 3 ? f2::dispatch_f32_f3(op, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s)
-                  : f2::dispatch_f32_f2(op, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
+        return F == 3 ? f2::dispatch_f64_f3(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s)
+                      : f2::dispatch_f64_f2(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
+    return F == 3 ? f2::dispatch_f32_f3(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s)
+                  : f2::dispatch_f32_f2(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
+}
+
+// In-place variant: X and Y only, dispersion factors from L2.
+bool ip_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
+{
+    if (logn != 14 && logn != 15)
+        return false;
+    const int LP = logn / 2, LQ = logn - LP;
+    if ((1 << LP) < C || (1 << LQ) < C)
+        return false;
+    const int A2 = (LP + 1) / 2, A1 = LP - A2;
+    const int Qc = (1 << LQ) / C;
+    const int nc = (1 << logn) / C;
+    const int maxT = 256;
+    int threads = threads_req;
+    if (threads == 0)
+        threads = std::min(maxT, (F * Qc * (1 << A1) + 31) / 32 * 32);
+    if (threads < 32 || threads > maxT || (threads & 31))
+        return false;
+    (void)A2;
+    const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
+    const int LS = (logn + 1) / 2;
+    size_t el = (size_t)F * nc * 2 + (1 << LQ) + (1 << LS) + ((1 << logn) >> LS);
+    size_t sm = el * csz + 32 * kNslot * sizeof(double);
+    if (sm > 227 * 1024)
+        return false;
+    if (dispatch(1, true, dbl, F, logn, nullptr, 0, C, threads, sm, false, 0, 0, 0, nullptr) < 1)
+        return false;
+    out->cluster = C;
+    out->threads = threads;
+    out->disp_in_smem = false;
+    out->smem = sm;
+    out->kernel = 3;
+    return true;
 }
 
 } // namespace
@@ -47,7 +81,7 @@ bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *
         size_t sm = el * csz + 32 * kNslot * sizeof(double);
         if (sm > 227 * 1024)
             continue;
-        if (dispatch(1, dbl, F, logn, nullptr, 0, C, threads, sm, ds == 1, 0, 0, 0, nullptr) < 1)
+        if (dispatch(1, false, dbl, F, logn, nullptr, 0, C, threads, sm, ds == 1, 0, 0, 0, nullptr) < 1)
             continue;
         out->cluster = C;
         out->threads = threads;
@@ -56,20 +90,22 @@ bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *
         out->kernel = 2;
         return true;
     }
-    return false;
+    // the three-buffer form does not fit: the in-place form holds twice the
+    // points per CTA
+    return ip_config(dbl, F, logn, C, threads_req, out);
 }
 
 int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg)
 {
-    return dispatch(1, dbl, F, logn, nullptr, 0, cfg.cluster, cfg.threads, cfg.smem,
-                    cfg.disp_in_smem, 0, 0, 0, nullptr);
+    return dispatch(1, cfg.kernel == 3, dbl, F, logn, nullptr, 0, cfg.cluster, cfg.threads,
+                    cfg.smem, cfg.disp_in_smem, 0, 0, 0, nullptr);
 }
 
 int fused2_launch(bool dbl, int F, int logn, const InstDesc *dd, int count, const FusedCfg &cfg,
                   int r_base, int chunk, int last, cudaStream_t s)
 {
-    return dispatch(0, dbl, F, logn, dd, count, cfg.cluster, cfg.threads, cfg.smem,
-                    cfg.disp_in_smem, r_base, chunk, last, s);
+    return dispatch(0, cfg.kernel == 3, dbl, F, logn, dd, count, cfg.cluster, cfg.threads,
+                    cfg.smem, cfg.disp_in_smem, r_base, chunk, last, s);
 }
 
 } // namespace opo

@@ -47,6 +47,20 @@ template <> struct F2Traits<double> {
     static constexpr int kSwz = 3; // 8 double2 per 128-byte bank row
 };
 
+// In-place variant (IP): only the X and Y buffers, so a CTA holds twice the
+// points of the S-buffer variant; dispersion factors come from L2.  Every
+// in-place stage permutes values within one column or one row, and the work
+// items of a column (row) are consecutive threads of one warp, so a warp
+// barrier between its reads and its writes is enough.  For that the column
+// buffer X is column-major under IP, and both buffers are XOR-swizzled with a
+// bit permutation of the column (row) index.
+template <class T> struct F2IpTraits;
+template <> struct F2IpTraits<float> {
+    static constexpr int kMaxThreads = 256;
+};
+template <> struct F2IpTraits<double> {
+    static constexpr int kMaxThreads = 256;
+};
 constexpr int kMaxCl = 16;
 
 template <int R, int DIR, class V>
@@ -55,8 +69,11 @@ __device__ __forceinline__ void dft_r(V *v)
     dft<R, DIR>(v);
 }
 
-template <class T, int F, int LP, int LQ>
-__global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
+template <class T, bool IP>
+constexpr int kF2MaxThreads = IP ? F2IpTraits<T>::kMaxThreads : F2Traits<T>::kMaxThreads;
+
+template <class T, int F, int LP, int LQ, bool IP>
+__global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     k_fused2(const InstDesc *__restrict__ descs, int r_base, int M, int write_out, int disp_smem)
 {
     using V = cv<T>;
@@ -80,8 +97,8 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *X = reinterpret_cast<V *>(smem_raw);
     V *Y = X + F * NC;
-    V *S = Y + F * NC;
-    V *Dsm = S + F * NC;
+    V *S = IP ? nullptr : Y + F * NC;
+    V *Dsm = IP ? Y + F * NC : S + F * NC;
     V *twQ = Dsm + (disp_smem ? F * NC : 0);
     V *twLo = twQ + Q;
     V *twHi = twLo + (1 << LS);
@@ -140,6 +157,21 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
     auto ridx = [=](int f, int row, int e) {
         return f * NC + (row << LQ) + (e ^ (((e >> SW) ^ (row << (SW - 1))) & SWM));
     };
+    // IP layouts: perm(x) puts neighbours x, x+1 in different halves of a
+    // 2^SW-element bank group and maps 2^SW aligned consecutive x to distinct
+    // values, so column (row) and cross-column (cross-row) accesses both avoid
+    // bank conflicts
+    auto perm = [](int x) {
+        return (((x & 1) << (SW - 1)) | ((x >> 1) & ((1 << (SW - 1)) - 1))) & SWM;
+    };
+    auto cidx_ip = [=](int f, int n1, int b) {
+        return f * NC + (b << LP) + (n1 ^ (((n1 >> SW) ^ perm(b)) & SWM));
+    };
+    auto ridx_ip = [=](int f, int row, int e) {
+        return f * NC + (row << LQ) + (e ^ (((e >> SW) ^ perm(row)) & SWM));
+    };
+    auto CI = [=](int f, int n1, int b) { return IP ? cidx_ip(f, n1, b) : cidx(f, n1, b); };
+    auto RI = [=](int f, int row, int e) { return IP ? ridx_ip(f, row, e) : ridx(f, row, e); };
     auto gtime = [=](int n1, int b) { return (n1 << LQ) + (c << logQc) + b; };
     auto twP = [&](int e) { return twQ[e << (LQ - LP)]; }; // W_P^e
     auto twN = [&](unsigned a) {
@@ -162,9 +194,20 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
         const V e0b = use_e ? ekz[qb] : cmk<V>((T)1, (T)0);
         const V e1b = use_e ? ekz[qb + 1] : e0b;
         const V e2b = use_e ? ekz[qb + 2] : e0b;
-        for (int u = threadIdx.x; u < (Qc << A2); u += blockDim.x) {
-            const int b = u & (Qc - 1), j = u >> logQc; // j < Ra2
-            V v[F][Ra1];
+        // work item u -> (column b, butterfly j < Ra2); IP keeps a column's
+        // items in consecutive threads
+        auto dec = [&](int u, int &b, int &j) {
+            if constexpr (IP) {
+                j = u & (Ra2 - 1);
+                b = u >> A2;
+            } else {
+                b = u & (Qc - 1);
+                j = u >> logQc;
+            }
+        };
+        auto load = [&](int u, V (&v)[F][Ra1]) {
+            int b, j;
+            dec(u, b, j);
             if constexpr (mode == 0) {
 #pragma unroll
                 for (int r = 0; r < Ra1; r++) {
@@ -174,12 +217,21 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
                         v[f][r] = gF[f * N + g];
                 }
             } else {
+                const V *src = IP ? X : S;
+#pragma unroll
+                for (int f = 0; f < F; f++)
+#pragma unroll
+                    for (int r = 0; r < Ra1; r++)
+                        v[f][r] = src[CI(f, j + r * Ra2, b)];
+            }
+        };
+        auto process = [&](int u, V (&v)[F][Ra1]) -> bool {
+            int b, j;
+            dec(u, b, j);
+            if constexpr (mode != 0) {
                 // inverse column stage 2: radix Ra1, Ns = Ra2, k = j
 #pragma unroll
                 for (int f = 0; f < F; f++) {
-#pragma unroll
-                    for (int r = 0; r < Ra1; r++)
-                        v[f][r] = S[cidx(f, j + r * Ra2, b)];
 #pragma unroll
                     for (int r = 1; r < Ra1; r++) {
                         V w = twP(r * j);
@@ -245,7 +297,7 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
 #pragma unroll
                         for (int f = 0; f < F; f++)
                             gF[f * N + gtime(j + r * Ra2, b)] = v[f][r];
-                    continue;
+                    return false;
                 }
             }
             if constexpr (mode == 0 || mode == 3) {
@@ -279,11 +331,43 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
             }
             // forward column stage 1: radix Ra1, Ns = 1, outputs at j Ra1 + r
 #pragma unroll
-            for (int f = 0; f < F; f++) {
+            for (int f = 0; f < F; f++)
                 dft_r<Ra1, -1>(v[f]);
+            return true;
+        };
+        auto store = [&](int u, V (&v)[F][Ra1]) {
+            int b, j;
+            dec(u, b, j);
+#pragma unroll
+            for (int f = 0; f < F; f++)
 #pragma unroll
                 for (int r = 0; r < Ra1; r++)
-                    X[cidx(f, j * Ra1 + r, b)] = v[f][r];
+                    X[CI(f, j * Ra1 + r, b)] = v[f][r];
+        };
+        if constexpr (IP && mode != 0) {
+            // in place on X: a column's reads and writes stay within one warp
+            const int items = Qc << A2;
+#pragma unroll 1
+            for (int base = 0; base < items; base += blockDim.x) {
+                // lanes past the end redo the last item and drop it, so the
+                // warp stays converged around the barrier
+                const int u0 = base + threadIdx.x;
+                const bool have = u0 < items;
+                const int u = have ? u0 : items - 1;
+                V v[F][Ra1];
+                load(u, v);
+                const bool st = process(u, v) && have;
+                __syncwarp();
+                if (st)
+                    store(u, v);
+                __syncwarp();
+            }
+        } else {
+            for (int u = threadIdx.x; u < (Qc << A2); u += blockDim.x) {
+                V v[F][Ra1];
+                load(u, v);
+                if (process(u, v))
+                    store(u, v);
             }
         }
     };
@@ -292,13 +376,22 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
     auto phase2 = [&]() {
         const int items = F * Qc * Ra1;
         for (int u = threadIdx.x; u < items; u += blockDim.x) {
-            const int b = u & (Qc - 1);
-            const int rest = u >> logQc;
-            const int j = rest & (Ra1 - 1), f = rest >> A1;
+            int b, j, f;
+            if constexpr (IP) {
+                j = u & (Ra1 - 1);
+                const int rest = u >> A1;
+                b = rest & (Qc - 1);
+                f = rest >> logQc;
+            } else {
+                b = u & (Qc - 1);
+                const int rest = u >> logQc;
+                j = rest & (Ra1 - 1);
+                f = rest >> A1;
+            }
             V v[Ra2];
 #pragma unroll
             for (int r = 0; r < Ra2; r++)
-                v[r] = X[cidx(f, j + r * Ra1, b)];
+                v[r] = X[CI(f, j + r * Ra1, b)];
 #pragma unroll
             for (int r = 1; r < Ra2; r++)
                 v[r] = cmul(v[r], twP(r * j));
@@ -310,41 +403,78 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
 #pragma unroll
             for (int r = 0; r < Ra2; r++) {
                 const int k1 = j + r * Ra1;
-                rY[k1 >> logPc][ridx(f, k1 & (Pc - 1), n2)] = cmul(v[r], w);
+                rY[k1 >> logPc][RI(f, k1 & (Pc - 1), n2)] = cmul(v[r], w);
                 w = cmul(w, step);
             }
         }
     };
 
-    // ---- phase 3: forward row stage 1, Y -> S
+    // ---- phase 3: forward row stage 1, Y -> S (in place on Y for IP)
     auto phase3 = [&]() {
         const int items = F * Pc * Rb2;
-        for (int u = threadIdx.x; u < items; u += blockDim.x) {
-            const int j = u & (Rb2 - 1);
+        auto dec = [&](int u, int &j, int &row, int &f) {
+            j = u & (Rb2 - 1);
             const int rest = u >> B2;
-            const int row = rest & (Pc - 1), f = rest >> logPc;
-            V v[Rb1];
+            row = rest & (Pc - 1);
+            f = rest >> logPc;
+        };
+        if constexpr (IP) {
+#pragma unroll 1
+            for (int base = 0; base < items; base += blockDim.x) {
+                const int u0 = base + threadIdx.x;
+                const bool have = u0 < items;
+                const int u = have ? u0 : items - 1;
+                int j, row, f;
+                V v[Rb1];
+                dec(u, j, row, f);
 #pragma unroll
-            for (int r = 0; r < Rb1; r++)
-                v[r] = Y[ridx(f, row, j + r * Rb2)];
-            dft_r<Rb1, -1>(v);
+                for (int r = 0; r < Rb1; r++)
+                    v[r] = Y[RI(f, row, j + r * Rb2)];
+                dft_r<Rb1, -1>(v);
+                __syncwarp();
+                if (have) {
 #pragma unroll
-            for (int r = 0; r < Rb1; r++)
-                S[ridx(f, row, j * Rb1 + r)] = v[r];
+                    for (int r = 0; r < Rb1; r++)
+                        Y[RI(f, row, j * Rb1 + r)] = v[r];
+                }
+                __syncwarp();
+            }
+        } else {
+            for (int u = threadIdx.x; u < items; u += blockDim.x) {
+                int j, row, f;
+                dec(u, j, row, f);
+                V v[Rb1];
+#pragma unroll
+                for (int r = 0; r < Rb1; r++)
+                    v[r] = Y[ridx(f, row, j + r * Rb2)];
+                dft_r<Rb1, -1>(v);
+#pragma unroll
+                for (int r = 0; r < Rb1; r++)
+                    S[ridx(f, row, j * Rb1 + r)] = v[r];
+            }
         }
     };
 
     // ---- block B: forward row stage 2, spectral factor, inverse row stage 1
     auto block_b = [&](bool cav, double *acc) {
         const int items = F * Pc * Rb1;
-        for (int u = threadIdx.x; u < items; u += blockDim.x) {
-            const int j = u & (Rb1 - 1);
+        const V *src = IP ? Y : S;
+        auto decode = [&](int u, int &j, int &row, int &f) {
+            j = u & (Rb1 - 1);
             const int rest = u >> B1;
-            const int row = rest & (Pc - 1), f = rest >> logPc;
-            V v[Rb2];
+            row = rest & (Pc - 1);
+            f = rest >> logPc;
+        };
+        auto load = [&](int u, V (&v)[Rb2]) {
+            int j, row, f;
+            decode(u, j, row, f);
 #pragma unroll
             for (int r = 0; r < Rb2; r++)
-                v[r] = S[ridx(f, row, j + r * Rb1)];
+                v[r] = src[RI(f, row, j + r * Rb1)];
+        };
+        auto finish = [&](int u, V (&v)[Rb2]) {
+            int j, row, f;
+            decode(u, j, row, f);
 #pragma unroll
             for (int r = 1; r < Rb2; r++)
                 v[r] = cmul(v[r], twQ[r * j]);
@@ -368,9 +498,35 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
                 v[r] = cmul(v[r], fac);
             }
             dft_r<Rb2, 1>(v);
+        };
+        auto store = [&](int u, V (&v)[Rb2]) {
+            int j, row, f;
+            decode(u, j, row, f);
 #pragma unroll
             for (int r = 0; r < Rb2; r++)
-                Y[ridx(f, row, j * Rb2 + r)] = v[r];
+                Y[RI(f, row, j * Rb2 + r)] = v[r];
+        };
+        if constexpr (IP) {
+#pragma unroll 1
+            for (int base = 0; base < items; base += blockDim.x) {
+                const int u0 = base + threadIdx.x;
+                const bool have = u0 < items;
+                const int u = have ? u0 : items - 1;
+                V v[Rb2];
+                load(u, v);
+                finish(u, v);
+                __syncwarp();
+                if (have)
+                    store(u, v);
+                __syncwarp();
+            }
+        } else {
+            for (int u = threadIdx.x; u < items; u += blockDim.x) {
+                V v[Rb2];
+                load(u, v);
+                finish(u, v);
+                store(u, v);
+            }
         }
     };
 
@@ -384,7 +540,7 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
             V v[Rb1];
 #pragma unroll
             for (int r = 0; r < Rb1; r++)
-                v[r] = Y[ridx(f, row, j + r * Rb2)];
+                v[r] = Y[RI(f, row, j + r * Rb2)];
 #pragma unroll
             for (int r = 1; r < Rb1; r++) {
                 V w = twQ[r * j];
@@ -401,27 +557,51 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
 #pragma unroll
             for (int r = 0; r < Rb1; r++) {
                 const int n2 = j + r * Rb2;
-                rX[n2 >> logQc][cidx(f, k1, n2 & (Qc - 1))] = cmul(v[r], w);
+                rX[n2 >> logQc][CI(f, k1, n2 & (Qc - 1))] = cmul(v[r], w);
                 w = cmul(w, step);
             }
         }
     };
 
-    // ---- phase 6: inverse column stage 1, X -> S
+    // ---- phase 6: inverse column stage 1, X -> S (in place on X for IP)
     auto phase6 = [&]() {
         const int items = F * Qc * Ra1;
-        for (int u = threadIdx.x; u < items; u += blockDim.x) {
-            const int b = u & (Qc - 1);
-            const int rest = u >> logQc;
-            const int j = rest & (Ra1 - 1), f = rest >> A1;
-            V v[Ra2];
+        if constexpr (IP) {
+#pragma unroll 1
+            for (int base = 0; base < items; base += blockDim.x) {
+                const int u0 = base + threadIdx.x;
+                const bool have = u0 < items;
+                const int u = have ? u0 : items - 1;
+                const int j = u & (Ra1 - 1);
+                const int rest = u >> A1;
+                const int b = rest & (Qc - 1), f = rest >> logQc;
+                V v[Ra2];
 #pragma unroll
-            for (int r = 0; r < Ra2; r++)
-                v[r] = X[cidx(f, j + r * Ra1, b)];
-            dft_r<Ra2, 1>(v);
+                for (int r = 0; r < Ra2; r++)
+                    v[r] = X[cidx_ip(f, j + r * Ra1, b)];
+                dft_r<Ra2, 1>(v);
+                __syncwarp();
+                if (have) {
 #pragma unroll
-            for (int r = 0; r < Ra2; r++)
-                S[cidx(f, j * Ra2 + r, b)] = v[r];
+                    for (int r = 0; r < Ra2; r++)
+                        X[cidx_ip(f, j * Ra2 + r, b)] = v[r];
+                }
+                __syncwarp();
+            }
+        } else {
+            for (int u = threadIdx.x; u < items; u += blockDim.x) {
+                const int b = u & (Qc - 1);
+                const int rest = u >> logQc;
+                const int j = rest & (Ra1 - 1), f = rest >> A1;
+                V v[Ra2];
+#pragma unroll
+                for (int r = 0; r < Ra2; r++)
+                    v[r] = X[cidx(f, j + r * Ra1, b)];
+                dft_r<Ra2, 1>(v);
+#pragma unroll
+                for (int r = 0; r < Ra2; r++)
+                    S[cidx(f, j * Ra2 + r, b)] = v[r];
+            }
         }
     };
 
@@ -470,11 +650,11 @@ __global__ void __launch_bounds__(F2Traits<T>::kMaxThreads, 1)
     }
 }
 
-template <class T, int F, int LP, int LQ>
+template <class T, int F, int LP, int LQ, bool IP>
 int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool disp_smem,
              int r_base, int chunk, int last, cudaStream_t s)
 {
-    auto kern = k_fused2<T, F, LP, LQ>;
+    auto kern = k_fused2<T, F, LP, LQ, IP>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t lc = {};
@@ -493,10 +673,10 @@ int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool 
     return e == cudaSuccess ? OPO_OK : OPO_E_CUDA;
 }
 
-template <class T, int F, int LP, int LQ>
+template <class T, int F, int LP, int LQ, bool IP>
 int max_active_t(int C, int threads, size_t sm)
 {
-    auto kern = k_fused2<T, F, LP, LQ>;
+    auto kern = k_fused2<T, F, LP, LQ, IP>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t lc = {};
@@ -519,35 +699,43 @@ int max_active_t(int C, int threads, size_t sm)
 }
 
 // Launch (op 0) or occupancy query (op 1) of every instantiated size for one
-// precision and field count; defined by the opo_fused2_*.cu units.
+// precision and field count; ip selects the in-place variant (2^14 and 2^15
+// only).  Defined by the opo_fused2_*.cu units.
 #define OPO_F2_DISPATCH_DECL(NAME)                                                               \
-    int NAME(int op, int logn, const InstDesc *dd, int count, int C, int threads, size_t sm,    \
-             bool ds, int r_base, int chunk, int last, cudaStream_t s)
+    int NAME(int op, bool ip, int logn, const InstDesc *dd, int count, int C, int threads,      \
+             size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
 OPO_F2_DISPATCH_DECL(dispatch_f32_f3);
 OPO_F2_DISPATCH_DECL(dispatch_f32_f2);
 OPO_F2_DISPATCH_DECL(dispatch_f64_f3);
 OPO_F2_DISPATCH_DECL(dispatch_f64_f2);
 
+#define OPO_F2_ONE(T, F, LP, LQ, IP)                                                             \
+    return op == 0 ? launch_t<T, F, LP, LQ, IP>(dd, count, C, threads, sm, ds, r_base, chunk,   \
+                                                last, s)                                         \
+                   : max_active_t<T, F, LP, LQ, IP>(C, threads, sm)
+
 #define OPO_F2_DISPATCH_DEF(NAME, T, F)                                                          \
     OPO_F2_DISPATCH_DECL(NAME)                                                                   \
     {                                                                                            \
+        if (ip) {                                                                                \
+            switch (logn) {                                                                      \
+            case 14:                                                                             \
+                OPO_F2_ONE(T, F, 7, 7, true);                                                    \
+            case 15:                                                                             \
+                OPO_F2_ONE(T, F, 7, 8, true);                                                    \
+            default:                                                                             \
+                return op == 0 ? OPO_E_UNSUPPORTED : 0;                                          \
+            }                                                                                    \
+        }                                                                                        \
         switch (logn) {                                                                          \
         case 12:                                                                                 \
-            return op == 0 ? launch_t<T, F, 6, 6>(dd, count, C, threads, sm, ds, r_base, chunk,  \
-                                                  last, s)                                       \
-                           : max_active_t<T, F, 6, 6>(C, threads, sm);                           \
+            OPO_F2_ONE(T, F, 6, 6, false);                                                       \
         case 13:                                                                                 \
-            return op == 0 ? launch_t<T, F, 6, 7>(dd, count, C, threads, sm, ds, r_base, chunk,  \
-                                                  last, s)                                       \
-                           : max_active_t<T, F, 6, 7>(C, threads, sm);                           \
-        case 14:                                                                                 \
-            return op == 0 ? launch_t<T, F, 7, 7>(dd, count, C, threads, sm, ds, r_base, chunk,  \
-                                                  last, s)                                       \
-                           : max_active_t<T, F, 7, 7>(C, threads, sm);                           \
+            OPO_F2_ONE(T, F, 6, 7, false);                                                       \
+        case 14:                                                                             \
+            OPO_F2_ONE(T, F, 7, 7, false);                                                       \
         case 15:                                                                                 \
-            return op == 0 ? launch_t<T, F, 7, 8>(dd, count, C, threads, sm, ds, r_base, chunk,  \
-                                                  last, s)                                       \
-                           : max_active_t<T, F, 7, 8>(C, threads, sm);                           \
+            OPO_F2_ONE(T, F, 7, 8, false);                                                       \
         default:                                                                                 \
             return op == 0 ? OPO_E_UNSUPPORTED : 0;                                              \
         }                                                                                        \

@@ -36,7 +36,7 @@ struct Derived {
 };
 
 struct FusedCfg {
-    int kernel = 1;      // 1: generic fused kernel, 2: size-specialised kernel
+    int kernel = 1;      // 1: generic, 2: size-specialised, 3: size-specialised in place
     int cluster;         // CTAs per instance
     int threads;         // threads per CTA
     int rt_per_launch;   // round trips per launch

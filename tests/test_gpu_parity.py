@@ -364,3 +364,51 @@ def test_specialised_fused_launch_shapes(cluster, threads):
         return
     compare(cfg, got, ref, opo.OPO_FP32_PH64, "C=%d T=%d" % (cluster, threads))
     assert got[3].cluster == cluster
+
+
+# ------------------------------ in-place specialised kernel (X and Y only)
+
+IP_CASES = [
+    ("sro_16384_c4", lambda: cfg_dispersive(n=16384, nz=3), opo.OPO_FP32_PH64, 4),
+    ("sync_16384_c4", lambda: cfg_sync(n=16384).replace(nz=3), opo.OPO_FP32_PH64, 4),
+    ("dro_32768_c8", lambda: cfg_dro(n=32768).replace(nz=2), opo.OPO_FP32_PH64, 8),
+    ("deg_16384_c4", lambda: cfg_degenerate(n=16384).replace(nz=3), opo.OPO_FP32_PH64, 4),
+    ("sro_16384_fp64_c8", lambda: cfg_dispersive(n=16384, nz=2), opo.OPO_FP64, 8),
+]
+
+
+@pytest.mark.parametrize("name,make,prec,cluster", IP_CASES, ids=[c[0] for c in IP_CASES])
+def test_inplace_kernel_round_trip(name, make, prec, cluster):
+    """Cluster sizes at which only the two-buffer (in-place) form fits."""
+    cfg = make()
+    a0 = strong(cfg, 2e6)
+    ref = oracle_rt(cfg, a0, m0=4)
+    got = gpu_rt(cfg, a0, prec, opo.OPO_PATH_FUSED, cluster=cluster, m0=4)
+    compare(cfg, got, ref, prec, name)
+    assert got[3].cluster == cluster
+
+
+def test_inplace_kernel_batch_and_resume_bitwise():
+    base = cfg_dispersive(n=16384, nz=3)
+    cfgs = [base, base.replace(delay=15e-15, pump_power=1.5 * base.pump_power)]
+    starts = [strong(c, 2e6, i) for i, c in enumerate(cfgs)]
+    alone = []
+    for c, a in zip(cfgs, starts):
+        with opo.Context(c, fields=a) as ctx:
+            ctx.set_path(opo.OPO_PATH_FUSED, 4, 2)
+            ctx.run(3)
+            alone.append((ctx.get_fields(), ctx.trace(3)))
+    ctxs = [opo.Context(c, fields=a) for c, a in zip(cfgs, starts)]
+    try:
+        for c in ctxs:
+            c.set_path(opo.OPO_PATH_FUSED, 4, 2)
+        b = opo.opo_batch_create([c.h for c in ctxs], 0, 0)
+        opo.opo_batch_run(b, 2)
+        opo.opo_batch_run(b, 1)
+        for ctx, (f, t) in zip(ctxs, alone):
+            assert np.array_equal(ctx.get_fields(), f)
+            assert np.array_equal(ctx.trace(1), t[2:])
+        opo.opo_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            c.close()
