@@ -276,7 +276,8 @@ def main():
 
     extras = {}
     if not args.skip_extras and rank == 0:
-        extras = single_and_plain(args, opo, W, base, prec, local, torch, cl_req, th_req)
+        # one instance alone: the default (latency-oriented) launch shape
+        extras = single_and_plain(args, opo, W, base, prec, local, torch)
         extras["e2e"] = e2e(args, opo, W, ctxs, batch, base, torch, np)
         extras["batched_sweep"] = sweep_leg(opo, W, prec, local, torch)
         extras["serving"] = serving_leg(prec, local, value, base)

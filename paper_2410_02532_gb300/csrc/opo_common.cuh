@@ -132,66 +132,78 @@ __host__ __device__ inline RadixPlan make_plan(int log2L)
 }
 
 // ------------------------------------------------------------- RK4 ----
-// Pointwise right-hand side of the nonlinear part of Eqs. (CEp)-(CEi).
-// e = e^{+i dk z}.  Two-field (degenerate) form: f_p = i(kappa_p/2) A_s^2
-// e^{-i dk z}, f_s = i kappa_s A_p A_s* e^{+i dk z}.
+// The nonlinear part of Eqs. (CEp)-(CEi) at one point is dA_x/dz = i c_x p_x
+// with the products (e = e^{+i dk z})
+//   three fields: p_p = A_s A_i e*, p_s = A_p A_i* e, p_i = A_p A_s* e,
+//                 c_x = kappa_x;
+//   two fields (degenerate): p_p = A_s^2 e*, p_s = A_p A_s* e,
+//                 c_p = kappa_p / 2, c_s = kappa_s.
+// One classic RK4 step of size h from z0 uses the products at the stage
+// points (stage factors e0 = e^{i dk z0}, e1 = e^{i dk (z0 + h/2)},
+// e2 = e^{i dk (z0 + h)}); the constants i c_x h/2, i c_x h and i c_x h/6 are
+// folded into the fused multiply-adds of the stage updates.
 template <int F, class V>
-__device__ __forceinline__ void nl_rhs(const V *a, V e, const typename cscal<V>::type *kap,
-                                       bool use_e, V *f)
+__device__ __forceinline__ void nl_prod(const V *a, V e, bool use_e, V *p)
 {
     if constexpr (F == 3) {
-        V sp = cmul(a[1], a[2]);        // A_s A_i
-        V ss = cmulc(a[0], a[2]);       // A_p A_i*
-        V si = cmulc(a[0], a[1]);       // A_p A_s*
+        p[0] = cmul(a[1], a[2]);  // A_s A_i
+        p[1] = cmulc(a[0], a[2]); // A_p A_i*
+        p[2] = cmulc(a[0], a[1]); // A_p A_s*
         if (use_e) {
-            sp = cmulc(sp, e);
-            ss = cmul(ss, e);
-            si = cmul(si, e);
+            p[0] = cmulc(p[0], e);
+            p[1] = cmul(p[1], e);
+            p[2] = cmul(p[2], e);
         }
-        f[0] = cscale(cmuli(sp), kap[0]);
-        f[1] = cscale(cmuli(ss), kap[1]);
-        f[2] = cscale(cmuli(si), kap[2]);
     } else {
-        V sp = cmul(a[1], a[1]);        // A_s^2
-        V ss = cmulc(a[0], a[1]);       // A_p A_s*
+        p[0] = cmul(a[1], a[1]);  // A_s^2
+        p[1] = cmulc(a[0], a[1]); // A_p A_s*
         if (use_e) {
-            sp = cmulc(sp, e);
-            ss = cmul(ss, e);
+            p[0] = cmulc(p[0], e);
+            p[1] = cmul(p[1], e);
         }
-        f[0] = cscale(cmuli(sp), kap[0] * (typename cscal<V>::type)0.5);
-        f[1] = cscale(cmuli(ss), kap[1]);
     }
 }
 
-// One classic RK4 step of size h from z0: stage factors e0 = e^{i dk z0},
-// e1 = e^{i dk (z0 + h/2)}, e2 = e^{i dk (z0 + h)}.
+// y + g (i p) for real g
+template <class V>
+__device__ __forceinline__ V add_ig(V y, typename cscal<V>::type g, V p)
+{
+    return cmk<V>(y.x - g * p.y, y.y + g * p.x);
+}
+
 template <int F, class V>
 __device__ __forceinline__ void rk4_point(V *y, V e0, V e1, V e2,
                                           const typename cscal<V>::type *kap,
                                           typename cscal<V>::type h, bool use_e)
 {
     using S = typename cscal<V>::type;
-    V k1[F], k2[F], k3[F], k4[F], t[F];
-    const S h2 = h * (S)0.5;
-    nl_rhs<F>(y, e0, kap, use_e, k1);
-#pragma unroll
-    for (int x = 0; x < F; x++)
-        t[x] = cmk<V>(y[x].x + h2 * k1[x].x, y[x].y + h2 * k1[x].y);
-    nl_rhs<F>(t, e1, kap, use_e, k2);
-#pragma unroll
-    for (int x = 0; x < F; x++)
-        t[x] = cmk<V>(y[x].x + h2 * k2[x].x, y[x].y + h2 * k2[x].y);
-    nl_rhs<F>(t, e1, kap, use_e, k3);
-#pragma unroll
-    for (int x = 0; x < F; x++)
-        t[x] = cmk<V>(y[x].x + h * k3[x].x, y[x].y + h * k3[x].y);
-    nl_rhs<F>(t, e2, kap, use_e, k4);
-    const S h6 = h / (S)6;
+    S c[F], ch[F], c6[F];
 #pragma unroll
     for (int x = 0; x < F; x++) {
-        S sx = k1[x].x + (S)2 * k2[x].x + (S)2 * k3[x].x + k4[x].x;
-        S sy = k1[x].y + (S)2 * k2[x].y + (S)2 * k3[x].y + k4[x].y;
-        y[x] = cmk<V>(y[x].x + h6 * sx, y[x].y + h6 * sy);
+        c[x] = (F == 2 && x == 0) ? kap[0] * (S)0.5 : kap[x];
+        ch[x] = c[x] * (h * (S)0.5);
+        c6[x] = c[x] * (h / (S)6);
+        c[x] = c[x] * h;
+    }
+    V p1[F], p2[F], p3[F], p4[F], t[F];
+    nl_prod<F>(y, e0, use_e, p1);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = add_ig(y[x], ch[x], p1[x]);
+    nl_prod<F>(t, e1, use_e, p2);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = add_ig(y[x], ch[x], p2[x]);
+    nl_prod<F>(t, e1, use_e, p3);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = add_ig(y[x], c[x], p3[x]);
+    nl_prod<F>(t, e2, use_e, p4);
+#pragma unroll
+    for (int x = 0; x < F; x++) {
+        S sx = p1[x].x + (S)2 * p2[x].x + (S)2 * p3[x].x + p4[x].x;
+        S sy = p1[x].y + (S)2 * p2[x].y + (S)2 * p3[x].y + p4[x].y;
+        y[x] = add_ig(y[x], c6[x], cmk<V>(sx, sy));
     }
 }
 
