@@ -159,7 +159,8 @@ OPO_API int opo_set_cavity(opo_ctx *ctx, const opo_cavity *cavity);
 
 /* Copy n complex values (2n interleaved doubles) into intracavity field
  * `field`; n must equal the grid's N.  rt_index >= 0 also sets the
- * round-trip counter m (the EOM phase depends on it); -1 leaves it. */
+ * round-trip counter m (the EOM phase depends on it) and clears a pending
+ * non-finite error (a new start); -1 leaves both. */
 OPO_API int opo_set_fields(opo_ctx *ctx, int32_t field, const double *interleaved, size_t n,
                    int64_t rt_index);
 

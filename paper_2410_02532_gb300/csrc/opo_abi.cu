@@ -453,8 +453,13 @@ static int set_fields_impl(opo_ctx *c, int32_t field, const void *src, size_t n,
     }
     if (e != cudaSuccess)
         return OPO_E_CUDA;
-    if (rt_index >= 0)
+    if (rt_index >= 0) {
+        // a new start: round-trip counter and the sticky non-finite flag
         c->rt = rt_index;
+        if (cudaMemsetAsync((char *)c->d_ctl + offsetof(DevCtl, err), 0, sizeof(int), c->stream) !=
+            cudaSuccess)
+            return OPO_E_CUDA;
+    }
     return OPO_OK;
 }
 

@@ -285,6 +285,19 @@ class Context:
             self.h = None
             raise
 
+    def reset(self, cfg, fields=None, pump_user=None, tod_div=0.0):
+        """Reuse this context (same N, field count, precision) for another
+        configuration: crystal, cavity and start fields are replaced and the
+        round-trip counter restarts at 0."""
+        if int(cfg.n) != self.n or int(cfg.nfields) != self.nfields:
+            raise ValueError("reset needs the same N and field count")
+        self.cfg = cfg
+        opo_set_crystal(self.h, crystal_from(cfg, tod_div))
+        cav, keep = cavity_from(cfg, pump_user)
+        opo_set_cavity(self.h, cav)
+        del keep
+        self.set_fields(cfg.initial_fields() if fields is None else fields, rt_index=0)
+
     def set_fields(self, fields, rt_index=-1):
         fields = np.asarray(fields, dtype=np.complex128).reshape(self.nfields, self.n)
         for x in range(self.nfields):

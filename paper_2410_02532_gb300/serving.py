@@ -4,10 +4,12 @@ Requests (an ``OPOConfig`` plus a round-trip budget M) arrive over time.
 Every tick the loop
 
 1. moves arrived requests into the wait queue;
-2. admits waiting requests first-come first-served while the SM budget (sum
-   of cluster sizes of active fused instances, plus a fixed share per plain
-   instance) and the device-memory budget allow: admission creates the
-   instance's device state, which then stays on the device until it retires;
+2. admits waiting requests first-come first-served while the GPU share and
+   the device-memory budget allow: a fused instance of a size class takes
+   1/capacity of the GPU, capacity being how many clusters of that class can
+   be resident at once (the library's occupancy query), a plain-path instance
+   a fixed share; admission configures device state that then stays on the
+   device until the request retires;
 3. advances every active instance by the same K round trips: all fused
    instances in one batched launch (grouped by size class inside the
    library), instances too large for the fused path on the plain path on their
@@ -30,9 +32,6 @@ import numpy as np
 
 from . import opo
 from . import workloads as W
-
-SMS = 152
-
 
 def instance_bytes(n, nfields, precision):
     """Device bytes of one context (fields, output, scratch, tables, staging)."""
@@ -75,37 +74,46 @@ class _Active:
         self.done = 0
         self.admitted = admitted
         self.trace = []
+        self.k = 0
 
 
 class Server:
     """Runs requests on one GPU with continuous batching.
 
-    ``tick_rt``: round trips per tick (latency granularity).  ``sm_budget``:
-    SMs the active fused instances may occupy (default: all).  ``hbm_budget``:
+    ``tick_rt``: round trips per tick (latency granularity).  ``gpu_share``:
+    fraction of the GPU the active instances may fill (1.0: as many as can be
+    resident at once).  ``hbm_budget``:
     device bytes for instance state (default: half of the free memory).
     ``launch``: optional callable ``(n, nfields, precision) -> (cluster,
     threads, rt_per_launch)`` (e.g. from the autotuner); default shapes
-    otherwise.
+    otherwise.  Device state of retired requests is kept in a pool per
+    (N, field count) and reconfigured for the next request of that class, so
+    admission allocates only when a class needs more instances than ever
+    before.  The loop is pipelined: while a tick runs on the GPU, arrivals
+    are admitted and prepared for the next tick.
     """
 
-    def __init__(self, precision=opo.OPO_FP32_PH64, device=0, tick_rt=16, sm_budget=SMS,
-                 hbm_budget=None, launch=None, plain_sm_share=16):
+    def __init__(self, precision=opo.OPO_FP32_PH64, device=0, tick_rt=16, gpu_share=1.0,
+                 hbm_budget=None, launch=None, plain_share=0.1):
         import torch
-        self.torch = torch
         self.precision = precision
         self.device = device
         self.tick_rt = int(tick_rt)
-        self.sm_budget = int(sm_budget)
+        self.gpu_share = float(gpu_share)
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info(device)
             hbm_budget = free // 2
         self.hbm_budget = int(hbm_budget)
         self.launch = launch
-        self.plain_sm_share = plain_sm_share
+        self.plain_share = float(plain_share)
+        self.capacity = {}  # (n, F, cluster, threads) -> resident clusters
         self.results = []
         self.ticks = 0
         self.busy_s = 0.0
         self.field_steps = 0.0
+        self.pool = collections.defaultdict(list)   # (n, F) -> idle contexts
+        self.pooled_bytes = 0
+        self.allocations = 0
 
     # ---------------------------------------------------------------- admission
     def _shape(self, cfg):
@@ -115,30 +123,49 @@ class Server:
                 return shape
         return (0, 0, 0)
 
-    def _admit(self, req, now, sm_used, mem_used):
-        cfg = req.cfg
-        need_mem = instance_bytes(cfg.n, cfg.nfields, self.precision)
-        if mem_used + need_mem > self.hbm_budget:
-            return None
+    def _context(self, cfg):
+        key = (cfg.n, cfg.nfields)
+        if self.pool[key]:
+            ctx = self.pool[key].pop()
+            self.pooled_bytes -= instance_bytes(cfg.n, cfg.nfields, self.precision)
+            ctx.reset(cfg)
+            return ctx
+        self.allocations += 1
         # a private stream per instance: plain-path instances overlap with the
         # batched fused launch, which fences each member's stream with events
-        ctx = opo.Context(cfg, precision=self.precision, device=self.device)
+        return opo.Context(cfg, precision=self.precision, device=self.device)
+
+    def _admit(self, req, now, share_used, mem_used):
+        cfg = req.cfg
+        need_mem = instance_bytes(cfg.n, cfg.nfields, self.precision)
+        pooled = bool(self.pool[(cfg.n, cfg.nfields)])
+        if not pooled and mem_used + self.pooled_bytes + need_mem > self.hbm_budget:
+            return None
+        ctx = self._context(cfg)
         cl, th, rtpl = self._shape(cfg)
         path, cluster = opo.OPO_PATH_FUSED, 0
         try:
             ctx.set_path(opo.OPO_PATH_FUSED, cl, rtpl, th)
-            _, cluster = opo.opo_fused_capacity(ctx.h, cl, th)
+            key = (cfg.n, cfg.nfields, cl, th)
+            if key not in self.capacity:
+                self.capacity[key] = opo.opo_fused_capacity(ctx.h, cl, th)
+            cap, cluster = self.capacity[key]
+            share = 1.0 / max(1, cap)
         except opo.OPOError:
             path, cluster = opo.OPO_PATH_PLAIN, 0
             ctx.set_path(opo.OPO_PATH_PLAIN)
-        share = cluster if path == opo.OPO_PATH_FUSED else self.plain_sm_share
-        if sm_used + share > self.sm_budget and sm_used > 0:
-            ctx.close()
+            share = self.plain_share
+        if share_used + share > self.gpu_share + 1e-9 and share_used > 0:
+            self._release(ctx, cfg)
             return None
         a = _Active(req, ctx, path, cluster, now)
         a.mem = need_mem
         a.share = share
         return a
+
+    def _release(self, ctx, cfg):
+        self.pool[(cfg.n, cfg.nfields)].append(ctx)
+        self.pooled_bytes += instance_bytes(cfg.n, cfg.nfields, self.precision)
 
     # -------------------------------------------------------------------- loop
     def run(self, requests, time_scale=1.0, clock=time.perf_counter, max_wall_s=None):
@@ -146,75 +173,98 @@ class Server:
         ``time_scale``) in real time; returns the list of ``Result``."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
-        active = []
-        sm_used = mem_used = 0
+        active, ready = [], []
+        budget = {"share": 0.0, "mem": 0}
         t0 = clock()
-        batch = None
-        batch_members = None
-        while pending or waiting or active:
+        batches = {}  # (k, member ids) -> batch handle
+
+        def admit():
             now = clock() - t0
-            if max_wall_s is not None and now > max_wall_s:
-                break
             while pending and pending[0].arrival * time_scale <= now:
                 waiting.append(pending.popleft())
             while waiting:
-                a = self._admit(waiting[0], now, sm_used, mem_used)
+                a = self._admit(waiting[0], now, budget["share"], budget["mem"])
                 if a is None:
                     break
                 waiting.popleft()
-                active.append(a)
-                sm_used += a.share
-                mem_used += a.mem
+                ready.append(a)
+                budget["share"] += a.share
+                budget["mem"] += a.mem
+
+        def drop_batches():
+            for b in batches.values():
+                opo.opo_batch_destroy(b)
+            batches.clear()
+
+        while pending or waiting or active or ready:
+            if max_wall_s is not None and clock() - t0 > max_wall_s:
+                break
+            admit()
+            active.extend(ready)
+            ready.clear()
             if not active:
                 if pending:
                     wait = pending[0].arrival * time_scale - (clock() - t0)
                     if wait > 0:
-                        time.sleep(min(wait, 0.01))
+                        time.sleep(min(wait, 0.005))
                 continue
-            k = min(self.tick_rt, min(a.req.rounds - a.done for a in active))
-            fused = [a for a in active if a.path == opo.OPO_PATH_FUSED]
-            plain = [a for a in active if a.path == opo.OPO_PATH_PLAIN]
-            members = tuple(id(a) for a in fused)
-            if members != batch_members:
-                if batch is not None:
-                    opo.opo_batch_destroy(batch)
-                batch = opo.opo_batch_create([a.ctx.h for a in fused], 0, 0) if fused else None
-                batch_members = members
+            # ---- launch one tick: instances finishing inside the tick run
+            # their remainder in a batch of their own
             t_tick = clock()
-            if batch is not None:
-                opo.opo_batch_run(batch, k)
-            for a in plain:
-                opo.opo_run_roundtrips(a.ctx.h, k)
+            groups = collections.defaultdict(list)
             for a in active:
-                a.trace.append(a.ctx.trace(k))  # waits for this instance's stream
+                a.k = min(self.tick_rt, a.req.rounds - a.done)
+                if a.path == opo.OPO_PATH_FUSED:
+                    groups[a.k].append(a)
+                else:
+                    opo.opo_run_roundtrips(a.ctx.h, a.k)
+            live = set()
+            for k, members in groups.items():
+                key = (k, tuple(id(a) for a in members))
+                live.add(key)
+                if key not in batches:
+                    batches[key] = opo.opo_batch_create([a.ctx.h for a in members], 0, 0)
+                opo.opo_batch_run(batches[key], k)
+            for key in [kk for kk in batches if kk not in live]:
+                opo.opo_batch_destroy(batches.pop(key))
+            # ---- while the GPU works: admit and prepare the next arrivals
+            admit()
+            # ---- finish the tick
+            for a in active:
+                a.trace.append(a.ctx.trace(a.k))  # waits for this instance's stream
             self.busy_s += clock() - t_tick
             self.ticks += 1
-            now = clock() - t0
-            if any(a.done + k >= a.req.rounds for a in active) and batch is not None:
-                # the batch points at its members: drop it before any retires
-                opo.opo_batch_destroy(batch)
-                batch, batch_members = None, None
+            finished = [a for a in active if a.done + a.k >= a.req.rounds]
+            if finished:
+                drop_batches()  # batches point at their members
             keep = []
             for a in active:
-                a.done += k
+                a.done += a.k
                 cfg = a.req.cfg
-                self.field_steps += cfg.nfields * cfg.nz * k
+                self.field_steps += cfg.nfields * cfg.nz * a.k
                 if a.done >= a.req.rounds:
                     out = a.ctx.get_fields(opo.OPO_OUTPUT)
                     self.results.append(Result(
                         a.req.rid, cfg.n, cfg.nfields, a.req.rounds, a.req.arrival * time_scale,
                         a.admitted, clock() - t0, a.path, out, np.concatenate(a.trace)))
-                    sm_used -= a.share
-                    mem_used -= a.mem
-                    a.ctx.close()
+                    budget["share"] -= a.share
+                    budget["mem"] -= a.mem
+                    self._release(a.ctx, cfg)
                 else:
                     keep.append(a)
             active = keep
-        if batch is not None:
-            opo.opo_batch_destroy(batch)
-        for a in active:
+        drop_batches()
+        for a in active + ready:
             a.ctx.close()
+        self.close()
         return self.results
+
+    def close(self):
+        for lst in self.pool.values():
+            for ctx in lst:
+                ctx.close()
+        self.pool.clear()
+        self.pooled_bytes = 0
 
 
 def latency_stats(results):
