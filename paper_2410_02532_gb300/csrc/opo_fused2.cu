@@ -28,7 +28,7 @@ bool ip_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
     const int A2 = (LP + 1) / 2, A1 = LP - A2;
     const int Qc = (1 << LQ) / C;
     const int nc = (1 << logn) / C;
-    const int maxT = 256;
+    const int maxT = dbl ? 256 : 384;
     int threads = threads_req;
     if (threads == 0)
         threads = std::min(maxT, (F * Qc * (1 << A1) + 31) / 32 * 32);

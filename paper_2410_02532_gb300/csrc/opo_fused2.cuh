@@ -56,7 +56,7 @@ template <> struct F2Traits<double> {
 // bit permutation of the column (row) index.
 template <class T> struct F2IpTraits;
 template <> struct F2IpTraits<float> {
-    static constexpr int kMaxThreads = 256;
+    static constexpr int kMaxThreads = 384;
 };
 template <> struct F2IpTraits<double> {
     static constexpr int kMaxThreads = 256;
@@ -225,7 +225,10 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                         v[f][r] = src[CI(f, j + r * Ra2, b)];
             }
         };
-        auto process = [&](int u, V (&v)[F][Ra1]) -> bool {
+        // own: this lane owns work item u (lanes past the end of the last
+        // round redo an item only to keep the warp converged; their
+        // observables must not count)
+        auto process = [&](int u, V (&v)[F][Ra1], bool own) -> bool {
             int b, j;
             dec(u, b, j);
             if constexpr (mode != 0) {
@@ -260,8 +263,9 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                 for (int r = 0; r < Ra1; r++) {
 #pragma unroll
                     for (int f = 0; f < F; f++) {
-                        acc[f] += (double)cabs2(v[f][r]);
-                        if (save_out)
+                        if (own)
+                            acc[f] += (double)cabs2(v[f][r]);
+                        if (save_out && own)
                             gOut[f * N + gtime(j + r * Ra2, b)] = cmul(v[f][r], osc[f]);
                     }
                 }
@@ -292,11 +296,13 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                     }
                 }
                 if (!next_rt) {
+                    if (own) {
 #pragma unroll
-                    for (int r = 0; r < Ra1; r++)
+                        for (int r = 0; r < Ra1; r++)
 #pragma unroll
-                        for (int f = 0; f < F; f++)
-                            gF[f * N + gtime(j + r * Ra2, b)] = v[f][r];
+                            for (int f = 0; f < F; f++)
+                                gF[f * N + gtime(j + r * Ra2, b)] = v[f][r];
+                    }
                     return false;
                 }
             }
@@ -356,7 +362,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                 const int u = have ? u0 : items - 1;
                 V v[F][Ra1];
                 load(u, v);
-                const bool st = process(u, v) && have;
+                const bool st = process(u, v, have) && have;
                 __syncwarp();
                 if (st)
                     store(u, v);
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
             for (int u = threadIdx.x; u < (Qc << A2); u += blockDim.x) {
                 V v[F][Ra1];
                 load(u, v);
-                if (process(u, v))
+                if (process(u, v, true))
                     store(u, v);
             }
         }
@@ -472,7 +478,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
             for (int r = 0; r < Rb2; r++)
                 v[r] = src[RI(f, row, j + r * Rb1)];
         };
-        auto finish = [&](int u, V (&v)[Rb2]) {
+        auto finish = [&](int u, V (&v)[Rb2], bool own) {
             int j, row, f;
             decode(u, j, row, f);
 #pragma unroll
@@ -487,7 +493,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                 V fac;
                 if (cav) {
                     fac = gG[f * N + k];
-                    if (f == 1) {
+                    if (f == 1 && own) {
                         double p2 = (double)cabs2(v[r]);
                         acc[3] += p2;
                         acc[4] += (double)((k < N / 2) ? k : k - N) * p2;
@@ -514,7 +520,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                 const int u = have ? u0 : items - 1;
                 V v[Rb2];
                 load(u, v);
-                finish(u, v);
+                finish(u, v, have);
                 __syncwarp();
                 if (have)
                     store(u, v);
@@ -524,7 +530,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
             for (int u = threadIdx.x; u < items; u += blockDim.x) {
                 V v[Rb2];
                 load(u, v);
-                finish(u, v);
+                finish(u, v, true);
                 store(u, v);
             }
         }
