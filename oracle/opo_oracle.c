@@ -29,7 +29,10 @@
  *   - non-resonant signal/idler restart from zero at every crystal entry;
  *   - z in e^{i dk z} is the position inside the crystal;
  *   - GDD is transformed back with the inverse transform;
- *   - the EOM phase uses tau_n = (n - N/2) dt plus m t_rt.
+ *   - the EOM phase uses tau_n = (n - N/2) dt plus m t_rt;
+ *   - a resonant pump (pump-resonant cavity) gets the input pump added at
+ *     entry; an ns-pulsed pump is a Gaussian in intensity read at
+ *     t = m t_rt + tau_n.
  * Parity unpinned (no printed values survive): the paper's figure curves,
  * its ns-pulsed example and its absolute threshold powers.
  */
@@ -273,6 +276,24 @@ void orc_cavity(const orc_params *p, double *fields, int64_t m)
     }
 }
 
+/* ---------------------------------------------------- ns-pulsed pump --- */
+
+/* Gaussian in intensity with FWHM ns_fwhm: A(t) = a0 exp(-2 ln 2 (t - t0)^2
+ * / fwhm^2), sampled at t = m t_rt + tau_n (Sec. 4.2: the long input pump
+ * is read one round trip at a time). */
+void orc_pump_slice(const orc_params *p, const double *pump_in, int64_t m, double *out)
+{
+    if (!(p->ns_fwhm > 0.0)) {
+        memcpy(out, pump_in, sizeof(double) * 2 * (size_t)p->n);
+        return;
+    }
+    for (int32_t j = 0; j < p->n; j++) {
+        double t = (double)m * p->t_rt + tau_of(p, j) - p->ns_t0;
+        out[2 * j] = p->ns_a0 * exp(-2.0 * log(2.0) * t * t / (p->ns_fwhm * p->ns_fwhm));
+        out[2 * j + 1] = 0.0;
+    }
+}
+
 /* ---------------------------------------------------------- round trip --- */
 
 static int all_finite(const double *v, size_t cnt)
@@ -290,15 +311,22 @@ int orc_run(const orc_params *p, double *fields, const double *pump_in,
     int F = p->nfields;
     size_t fsz = (size_t)2 * n;
     double *outbuf = (double *)malloc(sizeof(double) * fsz);
+    double *pump = (double *)malloc(sizeof(double) * fsz);
     for (int64_t r = 0; r < M; r++) {
         int64_t m = m0 + r;
-        /* entry: fresh pump if not resonant; non-resonant signal/idler from 0 */
+        /* entry: the input pump replaces a non-resonant pump and is added to a
+         * resonant one; non-resonant signal/idler restart from 0 */
+        orc_pump_slice(p, pump_in, m, pump);
         for (int x = 0; x < F; x++) {
-            if (p->resonant_mask & (1u << x))
-                continue;
             double *a = fields + fsz * x;
+            if (p->resonant_mask & (1u << x)) {
+                if (x == 0)
+                    for (size_t i = 0; i < fsz; i++)
+                        a[i] += pump[i];
+                continue;
+            }
             if (x == 0)
-                memcpy(a, pump_in, sizeof(double) * fsz);
+                memcpy(a, pump, sizeof(double) * fsz);
             else
                 memset(a, 0, sizeof(double) * fsz);
         }
@@ -320,10 +348,12 @@ int orc_run(const orc_params *p, double *fields, const double *pump_in,
             memcpy(trace + 4 * r, rec, sizeof(rec));
         if (!all_finite(fields, fsz * (size_t)F)) {
             free(outbuf);
+            free(pump);
             return 1;
         }
         orc_cavity(p, fields, m);
     }
     free(outbuf);
+    free(pump);
     return 0;
 }

@@ -56,6 +56,11 @@ typedef struct {
     double  eom_beta;       /* EOM depth beta [rad]                               */
     double  eom_f;          /* EOM frequency f_pm [Hz]                            */
     double  t_rt;           /* round-trip time for the EOM phase [s]              */
+    /* ns-pulsed pump (Sec. 4.2): a Gaussian much longer than t_rt, sliced
+     * per round trip; used instead of pump_in when ns_fwhm > 0 */
+    double  ns_a0;          /* peak field amplitude [V/m]                         */
+    double  ns_fwhm;        /* intensity FWHM [s]                                 */
+    double  ns_t0;          /* pulse centre on the round-trip time axis [s]       */
 } orc_params;
 
 /* In-place DFT of length n (power of two).  dir = -1: forward, unnormalized,
@@ -93,8 +98,14 @@ double orc_centroid(const orc_params *p, const double *a);
  * round trip m (GDD and delay, mirror, EOM). */
 void orc_cavity(const orc_params *p, double *fields, int64_t m);
 
+/* Input pump of round trip m (n complex): pump_in, or the slice
+ * t = m t_rt + tau_n of the ns-pulsed pump when ns_fwhm > 0. */
+void orc_pump_slice(const orc_params *p, const double *pump_in, int64_t m, double *out);
+
 /* Run round trips m0 .. m0+M-1.  fields: F*n complex, in/out (state at the
- * start of the next round trip).  pump_in: n complex.  trace (optional):
+ * start of the next round trip).  pump_in: n complex (ignored for an
+ * ns-pulsed pump).  Entry: a non-resonant pump is replaced by the input
+ * pump, a resonant pump (pump-resonant cavity) gets it added.  trace (optional):
  * M rows of {P_p_out, P_s_out, P_i_out, nu_c}.  out_fields (optional): F*n
  * complex output-coupled fields of the last round trip.  Returns 0, or 1 if a
  * non-finite value appeared (the run stops at that round trip). */

@@ -44,6 +44,9 @@ class Params(ctypes.Structure):
         ("eom_beta", ctypes.c_double),
         ("eom_f", ctypes.c_double),
         ("t_rt", ctypes.c_double),
+        ("ns_a0", ctypes.c_double),
+        ("ns_fwhm", ctypes.c_double),
+        ("ns_t0", ctypes.c_double),
     ]
 
 
@@ -71,6 +74,7 @@ def lib():
         L.orc_centroid.argtypes = [_P, _D]
         L.orc_centroid.restype = ctypes.c_double
         L.orc_cavity.argtypes = [_P, _D, ctypes.c_int64]
+        L.orc_pump_slice.argtypes = [_P, _D, ctypes.c_int64, _D]
         L.orc_run.argtypes = [_P, _D, _D, ctypes.c_int64, ctypes.c_int64, _D, _D]
         L.orc_run.restype = ctypes.c_int
         _lib = L
@@ -109,6 +113,11 @@ def params(cfg, tod_div=6.0):
     p.eom_beta = float(g("eom_beta"))
     p.eom_f = float(g("eom_f"))
     p.t_rt = float(g("t_rt", cfg.t_window))
+    if int(g("pump_kind", 0)) == 3:  # ns-pulsed pump
+        inten = float(cfg.pump_power) / (3.141592653589793 * p.w0 * p.w0)
+        p.ns_a0 = (2.0 * inten / (p.nidx[0] * 8.8541878128e-12 * 299792458.0)) ** 0.5
+        p.ns_fwhm = float(cfg.pump_fwhm)
+        p.ns_t0 = float(g("pump_t0"))
     return p
 
 
@@ -180,11 +189,19 @@ def cavity(p, fields, m=0):
     return a
 
 
+def pump_slice(p, pump_in, m):
+    out = np.zeros(p.n, dtype=np.complex128)
+    pin = _c(pump_in) if pump_in is not None else np.zeros(p.n, dtype=np.complex128)
+    lib().orc_pump_slice(ctypes.byref(p), _ptr(pin), int(m), _ptr(out))
+    return out
+
+
 def run(p, fields, pump_in, m0=0, M=1):
     """Round trips ``m0 .. m0+M-1``.  Returns ``(fields, trace, out_fields,
-    status)``; trace rows are ``(P_p, P_s, P_i, nu_c)``."""
+    status)``; trace rows are ``(P_p, P_s, P_i, nu_c)``.  ``pump_in`` may be
+    None for an ns-pulsed pump."""
     a = _c(fields).copy()
-    pin = _c(pump_in)
+    pin = _c(pump_in) if pump_in is not None else np.zeros(p.n, dtype=np.complex128)
     trace = np.zeros((max(int(M), 1), 4), dtype=np.float64)
     out = np.zeros_like(a)
     st = lib().orc_run(ctypes.byref(p), _ptr(a), _ptr(pin), int(m0), int(M),
@@ -193,5 +210,6 @@ def run(p, fields, pump_in, m0=0, M=1):
 
 
 __all__ = ["Params", "params", "fft", "kappa", "omega", "linear_step", "rk4_step",
-           "crystal_pass", "pump_profile", "power", "centroid", "cavity", "run", "lib"]
+           "crystal_pass", "pump_profile", "pump_slice", "power", "centroid", "cavity", "run",
+           "lib"]
 

@@ -35,6 +35,10 @@ MUTANTS = [
      "num += ((double)k / p->t_window) * pk + 0.0 * kk;"),
     ("sech width", "fwhm / (2.0 * acosh(sqrt(2.0)))", "fwhm / 1.665"),
     ("idler not dumped", "memset(a, 0, sizeof(double) * fsz);", "(void)a;"),
+    ("resonant pump not injected", "a[i] += pump[i];", "a[i] += 0.0 * pump[i];"),
+    ("ns pulse field FWHM", "exp(-2.0 * log(2.0) * t * t", "exp(-4.0 * log(2.0) * t * t"),
+    ("ns slice ignores round trip", "double t = (double)m * p->t_rt + tau_of(p, j)",
+     "double t = 0.0 * (double)m * p->t_rt + tau_of(p, j)"),
 ]
 
 

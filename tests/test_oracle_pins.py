@@ -402,6 +402,88 @@ def test_power_and_centroid(orc):
     assert abs(orc.power(p, 2, a) - ref) <= 1e-14 * ref
 
 
+# ------------------------- ns-pulsed pump and pump-resonant (TRO) entry
+
+def _ns_cfg(n=64, **kw):
+    base = dict(n=n, nz=4, length=5e-3, t_window=100e-12, nfields=2,
+                lam=(0.532e-6, 1.064e-6, 0.0), nidx=(2.23, 2.15, 1.0), deff=0.0,
+                pump_kind=W.PUMP_NS, pump_power=75.0, pump_fwhm=1e-9, pump_t0=2e-9)
+    base.update(kw)
+    return W.OPOConfig(**base)
+
+
+def test_ns_pump_slice_is_the_gaussian_read_per_round_trip(orc):
+    """Sec. 4.2: the long pump is read one round trip at a time.  Peak power
+    at t0, half the peak intensity at t0 +- FWHM/2 (the definition of the
+    intensity FWHM), and slice m covers t = m t_rt + tau_n."""
+    n, T = 64, 100e-12
+    cfg = _ns_cfg(n=n)
+    p = orc.params(cfg)
+    dt = T / n
+    # t0 = 2 ns = 20 round trips: tau_n = 0 (n = N/2) of slice 20 is the peak
+    a = orc.pump_slice(p, None, 20)
+    assert abs(orc.power(p, 0, np.full(n, a[n // 2])) - 75.0) <= 1e-12 * 75.0
+    # t0 + FWHM/2 = 2.5 ns = slice 25 at n = N/2 ; t0 - FWHM/2 = slice 15
+    for m in (15, 25):
+        b = orc.pump_slice(p, None, m)
+        assert abs(abs(b[n // 2]) ** 2 / abs(a[n // 2]) ** 2 - 0.5) <= 1e-13
+    # every sample: intensity 2^{-(2 (t - t0)/FWHM)^2}, field real and positive
+    for m in (0, 7, 19, 33):
+        b = orc.pump_slice(p, None, m)
+        t = m * T + (np.arange(n) - n / 2) * dt - 2e-9
+        ref = 0.5 ** ((2 * t / 1e-9) ** 2)
+        assert np.all(b.imag == 0) and np.all(b.real > 0)
+        assert np.max(np.abs(abs(b) ** 2 / abs(a[n // 2]) ** 2 - ref)) <= 1e-13
+    # the pump table is ignored in this mode
+    c = orc.pump_slice(p, np.full(n, 5.0 + 0j), 20)
+    assert np.array_equal(c, a)
+
+
+def test_ns_pump_output_trace_follows_the_pulse(orc):
+    """deff = 0, no loss or dispersion, pump not resonant: the output pump
+    power of round trip m is the pulse's mean power over that slice."""
+    n, T = 64, 100e-12
+    cfg = _ns_cfg(n=n)
+    p = orc.params(cfg)
+    A = np.zeros((2, n), complex)
+    _, trace, _, st = orc.run(p, A, None, 0, 40)
+    assert st == 0
+    dt = T / n
+    for m in range(40):
+        t = m * T + (np.arange(n) - n / 2) * dt - 2e-9
+        ref = 75.0 * np.mean(0.5 ** ((2 * t / 1e-9) ** 2))
+        assert abs(trace[m, 0] - ref) <= 1e-12 * 75.0
+    # resumed at round trip 17 the slices continue from m = 17
+    _, tr2, _, _ = orc.run(p, A, None, 17, 5)
+    assert np.array_equal(tr2, trace[17:22])
+
+
+def test_pump_resonant_entry_sums_a_geometric_series(orc):
+    """TRO entry (Sec. 4.2, pump resonant): the input pump is added to the
+    circulating pump, which the mirror scales by rho = sqrt(R) e^{i delta}
+    each round trip.  With deff = 0 the intracavity pump of round trip m is
+    A_in (1 - rho^{m+1}) / (1 - rho) and its output power
+    (1 - R) |1 - rho^{m+1}|^2 / |1 - rho|^2 P_in."""
+    Rp, dl = 0.9, 0.3
+    cfg = cw(n=8, deff=0.0, resonant_mask=0b111, R=(Rp, 0.98, 0.98), delta=(dl, 0.0, 0.0))
+    p = orc.params(cfg)
+    P = 3.0
+    pump = orc.pump_profile(p, 0, P)
+    A = np.zeros((3, 8), complex)
+    M = 60
+    out, trace, outf, st = orc.run(p, A, pump, 0, M)
+    assert st == 0
+    rho = math.sqrt(Rp) * complex(math.cos(dl), math.sin(dl))
+    for m in range(M):
+        g = abs(1 - rho ** (m + 1)) ** 2 / abs(1 - rho) ** 2
+        assert abs(trace[m, 0] - (1 - Rp) * g * P) <= 1e-12 * (1 - Rp) * g * P
+    # state after the last cavity: rho times the last round trip's pump
+    ref = pump[0] * rho * (1 - rho ** M) / (1 - rho)
+    assert np.max(np.abs(out[0] - ref)) <= 1e-12 * abs(ref)
+    assert np.allclose(outf[0], math.sqrt(1 - Rp) * pump[0] * (1 - rho ** M) / (1 - rho),
+                       rtol=1e-12, atol=0)
+
+
 # ------------------------------------------- 10-13. cavity-level physics
 
 @pytest.mark.parametrize("level", [0.9, 1.1, 2.0])
