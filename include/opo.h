@@ -4,10 +4,12 @@
  * arXiv 2410.02532 ("cuOPO").
  *
  * What one round trip computes (the paper's method):
- *   entry ........ the intracavity pump is replaced by the input pump unless
- *                  it is resonant (Sec. 4.1, pump read-in kernel); a
- *                  non-resonant signal/idler restarts from zero (Sec. 2.1,
- *                  boundary conditions apply to resonant fields only)
+ *   entry ........ the intracavity pump is replaced by the input pump
+ *                  (Sec. 4.1, pump read-in kernel), or, in a pump-resonant
+ *                  cavity (TRO, Sec. 4.2), the input pump is added to the
+ *                  circulating one; a non-resonant signal/idler restarts from
+ *                  zero (Sec. 2.1, boundary conditions apply to resonant
+ *                  fields only)
  *   crystal pass . nz fixed steps of the symmetrized split-step Fourier
  *                  method N/2 - L - N/2 (Sec. 2.2, Eq. (expon)) on the
  *                  coupled-wave equations (Sec. 2.1, Eqs. (CEp)-(CEi));
@@ -82,7 +84,11 @@ typedef enum {
 } opo_status;
 
 enum { OPO_FP64 = 0, OPO_FP32_PH64 = 1 };               /* opo_grid.precision */
-enum { OPO_PUMP_CW = 0, OPO_PUMP_SECH2 = 1, OPO_PUMP_USER = 2 };
+/* Input pump: CW; sech^2 pulse per round trip; a user profile per round
+ * trip; or the ns-pulsed regime (Sec. 4.2), a Gaussian in intensity much
+ * longer than a round trip, A(t) = A0 exp(-2 ln 2 (t - t0)^2 / fwhm^2), read
+ * at t = m t_rt + tau_n in round trip m. */
+enum { OPO_PUMP_CW = 0, OPO_PUMP_SECH2 = 1, OPO_PUMP_USER = 2, OPO_PUMP_NS = 3 };
 enum { OPO_INTRACAVITY = 0, OPO_OUTPUT = 1 };           /* opo_get_fields which */
 enum { OPO_PATH_AUTO = 0, OPO_PATH_PLAIN = 1, OPO_PATH_FUSED = 2 };
 
@@ -125,10 +131,12 @@ typedef struct {
     double  eom_beta_rad;    /* EOM depth beta (Sec. 2.3 item 2); 0 = no EOM       */
     double  eom_f_hz;        /* EOM frequency f_pm                                 */
     double  t_rt_s;          /* round-trip time in the EOM phase; 0 = t_window_s   */
-    int32_t pump_kind;       /* OPO_PUMP_CW / _SECH2 / _USER                        */
-    double  pump_power_W;    /* CW power, or sech^2 peak power                     */
-    double  pump_fwhm_s;     /* sech^2 intensity FWHM                              */
+    int32_t pump_kind;       /* OPO_PUMP_CW / _SECH2 / _USER / _NS                  */
+    double  pump_power_W;    /* CW power, or sech^2 / ns-pulse peak power          */
+    double  pump_fwhm_s;     /* sech^2 or ns-pulse intensity FWHM, > 0 for those   */
     const double *pump_user; /* OPO_PUMP_USER: 2N interleaved doubles [V/m], copied */
+    double  pump_t0_s;       /* OPO_PUMP_NS: pulse centre t0 on the axis m t_rt +
+                                tau_n (t_rt as for the EOM)                        */
 } opo_cavity;
 
 /* Result of opo_run_roundtrips (filled only when a pointer is passed, which

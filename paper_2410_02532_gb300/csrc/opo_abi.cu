@@ -120,6 +120,18 @@ int derive(opo_ctx *c)
     d.h = 0.5 * d.dz;
     d.use_dk = k.dk_per_m != 0.0;
     d.eom = v.eom_beta_rad != 0.0;
+    d.ns = NsPump{};
+    d.ns.n = c->n;
+    d.ns.dt = c->grid.t_window_s / (double)c->n;
+    d.ns.t_rt = v.t_rt_s > 0.0 ? v.t_rt_s : c->grid.t_window_s;
+    if (v.pump_kind == OPO_PUMP_NS) {
+        // peak power -> peak field: P = (1/2) n_p eps0 c |A|^2 pi w0^2
+        double intensity = v.pump_power_W / (kPi * k.w0_m * k.w0_m);
+        d.ns.a0 = std::sqrt(2.0 * intensity / (k.n[0] * kEps0 * kC0));
+        d.ns.c = 2.0 * std::log(2.0) / (v.pump_fwhm_s * v.pump_fwhm_s);
+        d.ns.t0 = v.pump_t0_s;
+        d.ns.on = 1;
+    }
     return OPO_OK;
 }
 
@@ -223,9 +235,11 @@ bool valid_cavity(const opo_ctx *c, const opo_cavity *v)
         !std::isfinite(v->t_rt_s) || v->t_rt_s < 0.0 || !std::isfinite(v->pump_power_W) ||
         v->pump_power_W < 0.0 || !std::isfinite(v->pump_fwhm_s))
         return false;
-    if (v->pump_kind < OPO_PUMP_CW || v->pump_kind > OPO_PUMP_USER)
+    if (v->pump_kind < OPO_PUMP_CW || v->pump_kind > OPO_PUMP_NS)
         return false;
-    if (v->pump_kind == OPO_PUMP_SECH2 && !(v->pump_fwhm_s > 0.0))
+    if (!std::isfinite(v->pump_t0_s))
+        return OPO_E_INVALID;
+    if ((v->pump_kind == OPO_PUMP_SECH2 || v->pump_kind == OPO_PUMP_NS) && !(v->pump_fwhm_s > 0.0))
         return false;
     if (v->pump_kind == OPO_PUMP_USER) {
         if (!v->pump_user)

@@ -283,6 +283,29 @@ __device__ __forceinline__ void stockham_stage_lr(int lr, const V *__restrict__ 
     }
 }
 
+// Entry pump of the ns-pulsed regime (Sec. 4.2): a Gaussian in intensity,
+// much longer than a round trip, read at t = m t_rt + tau_g,
+//   A = a0 exp(-c (t - t0)^2),  c = 2 ln 2 / fwhm^2.
+// The argument is formed in FP64; the exponential is taken in the field
+// precision.
+struct NsPump {
+    double a0, c, t0, t_rt, dt;
+    int n, on;
+};
+
+template <class T>
+__device__ __forceinline__ cv<T> ns_pump_at(const NsPump &q, int g, int64_t m)
+{
+    const double t = (double)m * q.t_rt + (double)(g - q.n / 2) * q.dt - q.t0;
+    const double x = q.c * t * t;
+    T a;
+    if constexpr (sizeof(T) == 8)
+        a = q.a0 * exp(-x);
+    else
+        a = (float)q.a0 * expf(-(float)x);
+    return cmk<cv<T>>(a, (T)0);
+}
+
 __host__ __device__ inline int ilog2(unsigned v)
 {
     int r = 0;

@@ -265,12 +265,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     for (int r = 0; r < M; r++) {
         const int64_t slot = (int64_t)r_base + r;
         const int64_t m = d.m_start + slot;
-        // ---- entry: fresh pump unless resonant; non-resonant s/i from zero
+        // ---- entry: the input pump replaces a non-resonant pump and is added
+        // to a resonant one; non-resonant s/i restart from zero
         for (int i = threadIdx.x; i < F * NC; i += blockDim.x) {
-            int f = i / NC;
-            if (d.resmask & (1u << f))
-                continue;
-            X[i] = (f == 0) ? gPump[gindex(i - f * NC)] : cmk<V>((T)0, (T)0);
+            const int f = i / NC;
+            const bool res = (d.resmask >> f) & 1u;
+            if (f == 0) {
+                const int g = gindex(i);
+                const V pin = d.ns.on ? ns_pump_at<T>(d.ns, g, m) : gPump[g];
+                X[i] = res ? cadd(X[i], pin) : pin;
+            } else if (!res) {
+                X[i] = cmk<V>((T)0, (T)0);
+            }
         }
         __syncthreads();
         // ---- crystal pass: nz symmetrized steps
@@ -490,6 +496,7 @@ void fill_desc(InstDesc &d, const opo_ctx *c)
     d.dt = c->grid.t_window_s / (double)c->n;
     d.t_window = c->grid.t_window_s;
     d.m_start = c->rt;
+    d.ns = c->dv.ns;
 }
 
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s)

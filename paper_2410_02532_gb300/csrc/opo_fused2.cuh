@@ -183,8 +183,8 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     // mode 0: first round trip of the launch, input from global memory
     // mode 1: interior z-step boundary
     // mode 2: end of the crystal pass (observables, then cavity forward)
-    // mode 3: end of the cavity visit (mirror, EOM, then entry of the next
-    //         round trip, or the final store)
+    // mode 3: end of the cavity visit of round trip m_cav (mirror, EOM, then
+    //         entry of round trip m_cav + 1, or the final store)
     auto block_a = [&](auto mode_tag, int qa, int qb, int64_t m_cav, bool next_rt, bool save_out,
                        double *acc) {
         constexpr int mode = decltype(mode_tag)::value;
@@ -312,11 +312,17 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                 for (int r = 0; r < Ra1; r++) {
                     V y[F];
 #pragma unroll
-                    for (int f = 0; f < F; f++) {
+                    for (int f = 0; f < F; f++)
                         y[f] = v[f][r];
+                    // the input pump replaces a non-resonant pump and is added
+                    // to a resonant one; non-resonant s/i restart from zero
+                    const int g = gtime(j + r * Ra2, b);
+                    const V pin = dg.ns.on ? ns_pump_at<T>(dg.ns, g, m_cav + 1) : gPump[g];
+                    y[0] = (resmask & 1u) ? cadd(y[0], pin) : pin;
+#pragma unroll
+                    for (int f = 1; f < F; f++)
                         if (!(resmask & (1u << f)))
-                            y[f] = (f == 0) ? gPump[gtime(j + r * Ra2, b)] : cmk<V>((T)0, (T)0);
-                    }
+                            y[f] = cmk<V>((T)0, (T)0);
                     rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
 #pragma unroll
                     for (int f = 0; f < F; f++)
@@ -632,7 +638,8 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     using M3 = std::integral_constant<int, 3>;
     cluster.sync(); // every CTA of the cluster is running; tables loaded
     double dummy[kNslot] = {0, 0, 0, 0, 0};
-    block_a(M0{}, 0, 0, 0, true, false, dummy);
+    // mode 0 enters round trip m_start + r_base (its m_cav is the one before)
+    block_a(M0{}, 0, 0, m_start + r_base - 1, true, false, dummy);
     for (int r = 0; r < M; r++) {
         const int64_t slot = (int64_t)r_base + r;
         const int64_t m = m_start + slot;

@@ -26,6 +26,7 @@ struct InstDesc {
     double eom_beta, eom_f, t_rt, dt, t_window;
     double pscale[3];  // n eps0 c / 2 * pi w0^2
     int64_t m_start;   // round-trip counter at the start of the call
+    NsPump ns;         // ns-pulsed pump (ns.on), replaces the pump table
 };
 
 // Observables of every instance and slot of the call: output power

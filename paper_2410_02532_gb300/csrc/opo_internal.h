@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/opo.h"
+#include "opo_common.cuh"
 
 namespace opo {
 
@@ -33,6 +34,7 @@ struct Derived {
     double pscale[3];    // n eps0 c / 2 * pi w0^2
     bool use_dk;
     bool eom;
+    NsPump ns;           // ns-pulsed pump parameters (ns.on = 0: pump table)
 };
 
 struct FusedCfg {

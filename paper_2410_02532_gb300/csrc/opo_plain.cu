@@ -19,14 +19,23 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Round-trip entry: the input pump (table, or the ns-pulsed pump read at
+// this round trip) replaces a non-resonant pump and is added to a resonant
+// one; non-resonant signal/idler restart from zero.
 template <class T>
-__global__ void k_entry(cv<T> *fields, const cv<T> *pump, int n, int F, unsigned resmask)
+__global__ void k_entry(cv<T> *fields, const cv<T> *pump, int n, int F, unsigned resmask,
+                        NsPump ns, const DevCtl *ctl)
 {
+    const int64_t m = ctl->rt0 + ctl->slot;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F * n; i += gridDim.x * blockDim.x) {
-        int x = i / n;
-        if (resmask & (1u << x))
-            continue;
-        fields[i] = (x == 0) ? pump[i] : cmk<cv<T>>((T)0, (T)0);
+        const int x = i / n;
+        const bool res = (resmask >> x) & 1u;
+        if (x == 0) {
+            const cv<T> pin = ns.on ? ns_pump_at<T>(ns, i, m) : pump[i];
+            fields[i] = res ? cadd(fields[i], pin) : pin;
+        } else if (!res) {
+            fields[i] = cmk<cv<T>>((T)0, (T)0);
+        }
     }
 }
 
@@ -313,7 +322,8 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
     const Derived &d = c->dv;
     const T h = (T)d.h;
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
-    k_entry<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_pump, n, F, c->cavity.resonant_mask);
+    k_entry<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_pump, n, F, c->cavity.resonant_mask,
+                                          c->dv.ns, c->d_ctl);
     const V *ekz = (const V *)c->d_ekz;
     for (int j = 0; j < c->crystal.nz; j++) {
         for (int half = 0; half < 2; half++) {

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libopo.so")
 OPO_OK, OPO_E_INVALID, OPO_E_NOMEM, OPO_E_CUDA = 0, 1, 2, 3
 OPO_E_NONFINITE, OPO_E_TIMEOUT, OPO_E_STATE, OPO_E_UNSUPPORTED = 4, 5, 6, 7
 OPO_FP64, OPO_FP32_PH64 = 0, 1
-OPO_PUMP_CW, OPO_PUMP_SECH2, OPO_PUMP_USER = 0, 1, 2
+OPO_PUMP_CW, OPO_PUMP_SECH2, OPO_PUMP_USER, OPO_PUMP_NS = 0, 1, 2, 3
 OPO_INTRACAVITY, OPO_OUTPUT = 0, 1
 OPO_PATH_AUTO, OPO_PATH_PLAIN, OPO_PATH_FUSED = 0, 1, 2
 
@@ -47,7 +47,8 @@ class Cavity(ctypes.Structure):
                 ("gdd_s2", _D3), ("delay_s", ctypes.c_double), ("eom_beta_rad", ctypes.c_double),
                 ("eom_f_hz", ctypes.c_double), ("t_rt_s", ctypes.c_double),
                 ("pump_kind", ctypes.c_int32), ("pump_power_W", ctypes.c_double),
-                ("pump_fwhm_s", ctypes.c_double), ("pump_user", ctypes.POINTER(ctypes.c_double))]
+                ("pump_fwhm_s", ctypes.c_double), ("pump_user", ctypes.POINTER(ctypes.c_double)),
+                ("pump_t0_s", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -256,6 +257,7 @@ def cavity_from(cfg, pump_user=None):
     v.pump_kind = cfg.pump_kind
     v.pump_power_W = cfg.pump_power
     v.pump_fwhm_s = cfg.pump_fwhm
+    v.pump_t0_s = getattr(cfg, "pump_t0", 0.0)
     keep = None
     if pump_user is not None:
         keep = _cplx_in(pump_user, cfg.n)

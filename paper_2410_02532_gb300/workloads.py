@@ -25,7 +25,7 @@ import numpy as np
 EPS0 = 8.8541878128e-12  # vacuum permittivity [F/m]
 C0 = 299792458.0         # speed of light [m/s]
 
-PUMP_CW, PUMP_SECH2, PUMP_USER = 0, 1, 2
+PUMP_CW, PUMP_SECH2, PUMP_USER, PUMP_NS = 0, 1, 2, 3
 
 _G = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -91,6 +91,7 @@ class OPOConfig:
     pump_kind: int = PUMP_CW
     pump_power: float = 1.0
     pump_fwhm: float = 0.0
+    pump_t0: float = 0.0
     noise_amp: float = 1e-15
     seed: int = 20241004
     instance: int = 0
@@ -180,6 +181,29 @@ def degenerate_2field(n: int = 1024, level: float = 2.0) -> OPOConfig:
     return c.replace(pump_power=level * sro_threshold_power(c))
 
 
+def ns_pulsed_degenerate(peak_w: float = 75.0, n: int = 1024) -> OPOConfig:
+    """ns-pulsed degenerate OPO (Sec. 4.2 example): 0.532 -> 1.064 um, 5 mm
+    crystal, 10 ns FWHM Gaussian pump of peak power ``peak_w`` (the paper's
+    examples use 75, 100 and 250 W), signal resonant, 100 ps round trip,
+    pulse centred at 30 ns, 600 round trips (60 ns).  Cavity length, waist
+    and mirror reflectivity of the paper's example are not given; these are
+    the defaults of the other presets."""
+    return degenerate_2field(n=n).replace(
+        name="ns_pulsed_n%d_2f_L5mm_nz50_%gW" % (n, peak_w), length=5e-3, nz=50,
+        pump_kind=PUMP_NS, pump_power=float(peak_w), pump_fwhm=10e-9, pump_t0=30e-9, M=600,
+        seed=20241009)
+
+
+def tro_cw(n: int = 1024, level: float = 0.05) -> OPOConfig:
+    """Triply resonant CW OPO (pump-resonant cavity, Sec. 4.2): 3 fields, 5 mm,
+    R = 0.9 / 0.98 / 0.98; the input pump is added to the circulating one each
+    round trip (cavity enhancement 1/(1 - sqrt R_p)^2 ~ 380 below threshold).
+    ``level`` is the input pump power in units of the SRO threshold."""
+    c = OPOConfig(name="tro_cw_n%d_3f_L5mm_nz50" % n, n=n, nz=50, length=5e-3,
+                  resonant_mask=0b111, R=(0.9, 0.98, 0.98), M=400, seed=20241010)
+    return c.replace(pump_power=level * sro_threshold_power(c.replace(resonant_mask=0b010)))
+
+
 def sweep_instances(count: int = 256, seed: int = 20241007) -> list:
     """Batched sweep: N log-uniform over 2^12..2^15, pump 1-5x threshold,
     timing mismatch within +-50 fs, L in 5-30 mm, 100 z-steps; 50% SRO 3-field,
@@ -212,8 +236,10 @@ PRESETS = {
     "cw_sro_16k": cw_sro_16k,
     "sync_pumped_64k": sync_pumped_64k,
     "degenerate_2field": degenerate_2field,
+    "ns_pulsed_degenerate": ns_pulsed_degenerate,
+    "tro_cw": tro_cw,
 }
 
 __all__ = ["OPOConfig", "noise", "sro_threshold_power", "PRESETS", "cw_sro_1024", "cw_sro_16k",
-           "sync_pumped_64k", "degenerate_2field", "sweep_instances", "EPS0", "C0",
-           "PUMP_CW", "PUMP_SECH2", "PUMP_USER"]
+           "sync_pumped_64k", "degenerate_2field", "ns_pulsed_degenerate", "tro_cw",
+           "sweep_instances", "EPS0", "C0", "PUMP_CW", "PUMP_SECH2", "PUMP_USER", "PUMP_NS"]

@@ -6,7 +6,8 @@ It runs one crystal pass on caller-owned device fields with all of its
 scratch in a fixed device array inside the library.  Here it is checked,
 through the C ABI and on two calls in a row, against the context API: a
 plain-path round trip whose cavity is transparent (every field resonant,
-R = 1, no detuning, GDD, delay or EOM) is exactly one crystal pass.  This file
+R = 1, no detuning, GDD, delay or EOM, no input pump) is exactly one crystal
+pass.  This file
 sorts last so that a run stopping at the first failure has run everything
 else first.
 """
@@ -38,8 +39,10 @@ def _rel_l2(a, b):
 
 
 def _transparent(cfg):
+    # a resonant pump gets the input pump added at entry: no input pump
     return cfg.replace(resonant_mask=(1 << cfg.nfields) - 1, R=(1.0, 1.0, 1.0),
-                       delta=(0.0, 0.0, 0.0), gdd=(0.0, 0.0, 0.0), delay=0.0, eom_beta=0.0)
+                       delta=(0.0, 0.0, 0.0), gdd=(0.0, 0.0, 0.0), delay=0.0, eom_beta=0.0,
+                       pump_power=0.0)
 
 
 def _context_passes(cfg, start, prec, count):
