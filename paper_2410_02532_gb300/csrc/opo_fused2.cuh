@@ -385,21 +385,15 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     };
 
     // ---- phase 2: forward column stage 2 and push into the owners' Y
+    // Consecutive lanes take consecutive columns b: each remote store of a
+    // warp then writes whole 128-byte runs of one destination row (the
+    // swizzles keep the column reads free of bank conflicts under IP too).
     auto phase2 = [&]() {
         const int items = F * Qc * Ra1;
         for (int u = threadIdx.x; u < items; u += blockDim.x) {
-            int b, j, f;
-            if constexpr (IP) {
-                j = u & (Ra1 - 1);
-                const int rest = u >> A1;
-                b = rest & (Qc - 1);
-                f = rest >> logQc;
-            } else {
-                b = u & (Qc - 1);
-                const int rest = u >> logQc;
-                j = rest & (Ra1 - 1);
-                f = rest >> A1;
-            }
+            const int b = u & (Qc - 1);
+            const int rest = u >> logQc;
+            const int j = rest & (Ra1 - 1), f = rest >> A1;
             V v[Ra2];
 #pragma unroll
             for (int r = 0; r < Ra2; r++)
@@ -543,12 +537,25 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     };
 
     // ---- phase 5: inverse row stage 2 and push into the owners' X
+    // The destination X is row-major without IP (consecutive lanes take
+    // consecutive butterflies j, i.e. consecutive columns n2) and column-major
+    // with IP (consecutive lanes take consecutive rows k1); either way a warp's
+    // remote store writes whole 128-byte runs.
     auto phase5 = [&]() {
         const int items = F * Pc * Rb2;
         for (int u = threadIdx.x; u < items; u += blockDim.x) {
-            const int j = u & (Rb2 - 1);
-            const int rest = u >> B2;
-            const int row = rest & (Pc - 1), f = rest >> logPc;
+            int j, row, f;
+            if constexpr (IP) {
+                row = u & (Pc - 1);
+                const int rest = u >> logPc;
+                j = rest & (Rb2 - 1);
+                f = rest >> B2;
+            } else {
+                j = u & (Rb2 - 1);
+                const int rest = u >> B2;
+                row = rest & (Pc - 1);
+                f = rest >> logPc;
+            }
             V v[Rb1];
 #pragma unroll
             for (int r = 0; r < Rb1; r++)
