@@ -87,6 +87,7 @@ int blocks(int64_t work)
 void free_all(opo_ctx *c)
 {
     void *bufs[] = {c->d_fields, c->d_out, c->d_scratch, c->d_pump, c->d_disp, c->d_gdd,
+                    c->d_disp_t, c->d_gdd_t,
                     c->d_tw, c->d_ekz, c->d_pump_user, c->d_obs, c->d_trace, c->d_ctl,
                     c->d_stage};
     for (void *b : bufs)
@@ -340,6 +341,8 @@ int opo_create(opo_ctx **out, const opo_grid *grid)
     alloc(&c->d_scratch, fb);
     alloc(&c->d_disp, fb);
     alloc(&c->d_gdd, fb);
+    alloc(&c->d_disp_t, fb);
+    alloc(&c->d_gdd_t, fb);
     alloc(&c->d_pump, c->csz * c->n);
     alloc(&c->d_tw, c->csz * c->n);
     alloc((void **)&c->d_pump_user, sizeof(double) * 2 * c->n);

@@ -468,6 +468,8 @@ void fill_desc(InstDesc &d, const opo_ctx *c)
     d.pump = c->d_pump;
     d.disp = c->d_disp;
     d.gdd = c->d_gdd;
+    d.disp_t = c->d_disp_t;
+    d.gdd_t = c->d_gdd_t;
     d.tw = c->d_tw;
     d.ekz = c->d_ekz;
     d.obs = c->d_obs;

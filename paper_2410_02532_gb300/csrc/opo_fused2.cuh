@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     const V *gPump = (const V *)dg.pump;
     const V *gD = (const V *)dg.disp;
     const V *gG = (const V *)dg.gdd;
+    const V *gDt = (const V *)dg.disp_t;
+    const V *gGt = (const V *)dg.gdd_t;
     const V *ekz = (const V *)dg.ekz;
     const V *gtw = (const V *)dg.tw;
     double *obs = dg.obs;
@@ -481,27 +483,36 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
         auto finish = [&](int u, V (&v)[Rb2], bool own) {
             int j, row, f;
             decode(u, j, row, f);
+            const int k1 = (c << logPc) + row;
+            // IP: the factors come from L2, from the row-major copy, so that
+            // a warp's loads (consecutive j) coalesce; issued before the
+            // transform so that their latency overlaps it
+            V fac[IP ? Rb2 : 1];
+            if constexpr (IP) {
+                const V *tab = (cav ? gGt : gDt) + f * N + (k1 << LQ) + j;
+#pragma unroll
+                for (int r = 0; r < Rb2; r++)
+                    fac[r] = tab[r * Rb1];
+            }
 #pragma unroll
             for (int r = 1; r < Rb2; r++)
                 v[r] = cmul(v[r], twQ[r * j]);
             dft_r<Rb2, -1>(v);
-            const int k1 = (c << logPc) + row;
 #pragma unroll
             for (int r = 0; r < Rb2; r++) {
                 const int k2 = j + r * Rb1;
                 const int k = k1 + (k2 << LP);
-                V fac;
-                if (cav) {
-                    fac = gG[f * N + k];
-                    if (f == 1 && own) {
-                        double p2 = (double)cabs2(v[r]);
-                        acc[3] += p2;
-                        acc[4] += (double)((k < N / 2) ? k : k - N) * p2;
-                    }
-                } else {
-                    fac = disp_smem ? Dsm[f * NC + (row << LQ) + k2] : gD[f * N + k];
+                V d;
+                if constexpr (IP)
+                    d = fac[r];
+                else
+                    d = cav ? gG[f * N + k] : (disp_smem ? Dsm[f * NC + (row << LQ) + k2] : gD[f * N + k]);
+                if (cav && f == 1 && own) {
+                    double p2 = (double)cabs2(v[r]);
+                    acc[3] += p2;
+                    acc[4] += (double)((k < N / 2) ? k : k - N) * p2;
                 }
-                v[r] = cmul(v[r], fac);
+                v[r] = cmul(v[r], d);
             }
             dft_r<Rb2, 1>(v);
         };

@@ -13,6 +13,8 @@ struct InstDesc {
     const void *pump;  // N input pump
     const void *disp;  // F*N dispersion factors / N (natural order)
     const void *gdd;   // F*N cavity spectral factors / N (natural order)
+    const void *disp_t; // the same two tables row-major over N = P Q:
+    const void *gdd_t;  //   [x][k1][k2] holds bin k1 + k2 P
     const void *tw;    // N twiddles W_N^j
     const void *ekz;   // 4 nz + 1 factors e^{i dk q dz/4}
     double *obs;       // raw sums of slot 0 of this call: [slot][C][kNslot]

@@ -66,6 +66,11 @@ struct opo_ctx {
     void *d_pump = nullptr;    // N input pump
     void *d_disp = nullptr;    // F*N dispersion factors / N, natural order
     void *d_gdd = nullptr;     // F*N cavity spectral factors / N, natural order
+    // the same two tables row-major over N = P Q, P = 2^(logn/2): entry
+    // [x][k1][k2] holds bin k = k1 + k2 P (the order in which the in-place
+    // fused kernel visits a row spectrum, so that its loads coalesce)
+    void *d_disp_t = nullptr;
+    void *d_gdd_t = nullptr;
     void *d_tw = nullptr;      // N twiddles W_N^j = e^{-2 pi i j/N}
     void *d_ekz = nullptr;     // 4 nz + 1 factors e^{i dk q dz/4}
     int ekz_cap = 0;

@@ -35,8 +35,16 @@ __device__ __forceinline__ double omega_k(int k, int n, double t_window)
     return 2.0 * kPi * (double)kk / t_window;
 }
 
+// Index of bin k of field x in the row-major copy: [x][k1][k2], k = k1 + k2 P.
+__device__ __forceinline__ int rowmajor_index(int x, int k, int n, int logP)
+{
+    const int logQ = ilog2((unsigned)n) - logP;
+    return x * n + ((k & ((1 << logP) - 1)) << logQ) + (k >> logP);
+}
+
+// Dt (optional): the row-major copy, over N = 2^logP x N/2^logP.
 template <class T>
-__global__ void k_disp_table(cv<T> *D, int n, int F, DispArgs a)
+__global__ void k_disp_table(cv<T> *D, cv<T> *Dt, int logP, int n, int F, DispArgs a)
 {
     const double inv_n = 1.0 / (double)n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F * n; i += gridDim.x * blockDim.x) {
@@ -47,7 +55,10 @@ __global__ void k_disp_table(cv<T> *D, int n, int F, DispArgs a)
         double amp = exp(-a.alpha[x] * a.dz * 0.5) * inv_n;
         double s, c;
         sincos(ph, &s, &c);
-        D[i] = cmk<cv<T>>((T)(amp * c), (T)(amp * s));
+        const cv<T> d = cmk<cv<T>>((T)(amp * c), (T)(amp * s));
+        D[i] = d;
+        if (Dt)
+            Dt[rowmajor_index(x, k, n, logP)] = d;
     }
 }
 
@@ -58,7 +69,7 @@ struct GddArgs {
 };
 
 template <class T>
-__global__ void k_gdd_table(cv<T> *G, int n, int F, GddArgs a)
+__global__ void k_gdd_table(cv<T> *G, cv<T> *Gt, int logP, int n, int F, GddArgs a)
 {
     const double inv_n = 1.0 / (double)n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F * n; i += gridDim.x * blockDim.x) {
@@ -70,7 +81,9 @@ __global__ void k_gdd_table(cv<T> *G, int n, int F, GddArgs a)
         }
         double s, c;
         sincos(ph, &s, &c);
-        G[i] = cmk<cv<T>>((T)(c * inv_n), (T)(s * inv_n));
+        const cv<T> g = cmk<cv<T>>((T)(c * inv_n), (T)(s * inv_n));
+        G[i] = g;
+        Gt[rowmajor_index(x, k, n, logP)] = g;
     }
 }
 
@@ -154,12 +167,12 @@ int setup_crystal_tables(opo_ctx *c)
     int cnt = 4 * k.nz + 1;
     if (c->prec == OPO_FP64) {
         k_disp_table<double><<<grid_for((int64_t)c->F * c->n), 256, 0, c->stream>>>(
-            (double2 *)c->d_disp, c->n, c->F, a);
+            (double2 *)c->d_disp, (double2 *)c->d_disp_t, c->logn / 2, c->n, c->F, a);
         k_ekz_table<double><<<grid_for(cnt), 256, 0, c->stream>>>((double2 *)c->d_ekz, cnt,
                                                                    k.dk_per_m, a.dz);
     } else {
         k_disp_table<float><<<grid_for((int64_t)c->F * c->n), 256, 0, c->stream>>>(
-            (float2 *)c->d_disp, c->n, c->F, a);
+            (float2 *)c->d_disp, (float2 *)c->d_disp_t, c->logn / 2, c->n, c->F, a);
         k_ekz_table<float><<<grid_for(cnt), 256, 0, c->stream>>>((float2 *)c->d_ekz, cnt,
                                                                   k.dk_per_m, a.dz);
     }
@@ -181,13 +194,13 @@ int setup_cavity_tables(opo_ctx *c)
     double dt = c->grid.t_window_s / (double)c->n;
     if (c->prec == OPO_FP64) {
         k_gdd_table<double><<<grid_for((int64_t)c->F * c->n), 256, 0, c->stream>>>(
-            (double2 *)c->d_gdd, c->n, c->F, g);
+            (double2 *)c->d_gdd, (double2 *)c->d_gdd_t, c->logn / 2, c->n, c->F, g);
         k_pump<double><<<grid_for(c->n), 256, 0, c->stream>>>((double2 *)c->d_pump, c->n,
                                                                 v.pump_kind, a0, t0, dt,
                                                                 c->d_pump_user);
     } else {
         k_gdd_table<float><<<grid_for((int64_t)c->F * c->n), 256, 0, c->stream>>>(
-            (float2 *)c->d_gdd, c->n, c->F, g);
+            (float2 *)c->d_gdd, (float2 *)c->d_gdd_t, c->logn / 2, c->n, c->F, g);
         k_pump<float><<<grid_for(c->n), 256, 0, c->stream>>>((float2 *)c->d_pump, c->n,
                                                                v.pump_kind, a0, t0, dt,
                                                                c->d_pump_user);
@@ -211,11 +224,11 @@ int setup_pass_tables(void *tw, void *disp, void *ekz, int n, int F, bool dbl,
     const int cnt = 4 * k.nz + 1;
     if (dbl) {
         k_twiddles<double><<<grid_for(n), 256, 0, s>>>((double2 *)tw, n);
-        k_disp_table<double><<<grid_for((int64_t)F * n), 256, 0, s>>>((double2 *)disp, n, F, a);
+        k_disp_table<double><<<grid_for((int64_t)F * n), 256, 0, s>>>((double2 *)disp, nullptr, 0, n, F, a);
         k_ekz_table<double><<<grid_for(cnt), 256, 0, s>>>((double2 *)ekz, cnt, k.dk_per_m, a.dz);
     } else {
         k_twiddles<float><<<grid_for(n), 256, 0, s>>>((float2 *)tw, n);
-        k_disp_table<float><<<grid_for((int64_t)F * n), 256, 0, s>>>((float2 *)disp, n, F, a);
+        k_disp_table<float><<<grid_for((int64_t)F * n), 256, 0, s>>>((float2 *)disp, nullptr, 0, n, F, a);
         k_ekz_table<float><<<grid_for(cnt), 256, 0, s>>>((float2 *)ekz, cnt, k.dk_per_m, a.dz);
     }
     return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;

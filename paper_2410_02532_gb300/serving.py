@@ -36,7 +36,7 @@ from . import workloads as W
 def instance_bytes(n, nfields, precision):
     """Device bytes of one context (fields, output, scratch, tables, staging)."""
     csz = 16 if precision == opo.OPO_FP64 else 8
-    return csz * n * (5 * nfields + 2) + 16 * 2 * n * 2 + 4096 * 8 * 4
+    return csz * n * (7 * nfields + 2) + 16 * 2 * n * 2 + 4096 * 8 * 4
 
 
 @dataclasses.dataclass
