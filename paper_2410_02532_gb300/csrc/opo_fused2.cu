@@ -28,7 +28,7 @@ bool ip_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
     const int A2 = (LP + 1) / 2, A1 = LP - A2;
     const int Qc = (1 << LQ) / C;
     const int nc = (1 << logn) / C;
-    const int maxT = dbl ? 256 : 384;
+    const int maxT = dbl ? 256 : 512;
     int threads = threads_req;
     if (threads == 0)
         threads = std::min(maxT, (F * Qc * (1 << A1) + 31) / 32 * 32);
@@ -53,10 +53,10 @@ bool ip_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
 
 } // namespace
 
-bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
+namespace {
+
+bool three_buffer_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
-    if (logn < 12 || logn > 15)
-        return false;
     const int LP = logn / 2, LQ = logn - LP;
     if ((1 << LP) < C || (1 << LQ) < C)
         return false;
@@ -90,9 +90,33 @@ bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *
         out->kernel = 2;
         return true;
     }
-    // the three-buffer form does not fit: the in-place form holds twice the
-    // points per CTA
-    return ip_config(dbl, F, logn, C, threads_req, out);
+    return false;
+}
+
+} // namespace
+
+// Of the two forms that can run (N, F, C, threads), take the one with more
+// clusters co-resident on the device (the in-place form holds twice the
+// points per CTA, so where both fit it usually packs two CTAs per SM); on a
+// tie the three-buffer form, which keeps the dispersion factors in shared
+// memory.
+bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
+{
+    if (logn < 12 || logn > 15)
+        return false;
+    FusedCfg a, b;
+    const bool ok_a = three_buffer_config(dbl, F, logn, C, threads_req, &a);
+    const bool ok_b = ip_config(dbl, F, logn, C, threads_req, &b);
+    if (!ok_a && !ok_b)
+        return false;
+    if (ok_a && ok_b) {
+        const int na = fused2_max_active(dbl, F, logn, a);
+        const int nb = fused2_max_active(dbl, F, logn, b);
+        *out = nb > na ? b : a;
+    } else {
+        *out = ok_a ? a : b;
+    }
+    return true;
 }
 
 int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg)

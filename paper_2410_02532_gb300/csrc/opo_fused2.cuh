@@ -56,7 +56,7 @@ template <> struct F2Traits<double> {
 // bit permutation of the column (row) index.
 template <class T> struct F2IpTraits;
 template <> struct F2IpTraits<float> {
-    static constexpr int kMaxThreads = 384;
+    static constexpr int kMaxThreads = 512; // 16 warps per SM at <= 128 registers
 };
 template <> struct F2IpTraits<double> {
     static constexpr int kMaxThreads = 256;

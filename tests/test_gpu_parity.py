@@ -347,7 +347,8 @@ def test_specialised_batch_and_resume_bitwise():
             c.close()
 
 
-@pytest.mark.parametrize("cluster,threads", [(8, 256), (16, 192), (16, 384), (4, 384), (4, 320), (4, 256)])
+@pytest.mark.parametrize("cluster,threads", [(8, 256), (16, 192), (16, 384), (4, 384), (4, 320),
+                                            (4, 256), (4, 512), (8, 128), (8, 384)])
 def test_specialised_fused_launch_shapes(cluster, threads):
     """The same round trip under other cluster and CTA sizes (the autotuner's
     search space) stays within tolerance of the oracle."""
