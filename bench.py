@@ -33,6 +33,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SSFM field-steps/s at N=2^14 (fused, batched round trips)"
+# (instances, cluster, threads requested) -> DRAM bytes per fused launch of the
+# 2^14 workload (48.13 MB read + 1.03 MB written; threads 0 = the library's
+# default, 512, for this shape)
+PROFILED_SHAPES = {(36, 4, 0): 49.159424e6, (36, 4, 512): 49.159424e6}
 UNIT = "field-steps/s"
 PEAK_SM_MHZ = 2070.0          # GB300 maximum SM clock
 SMS = 152
@@ -265,11 +269,17 @@ def main():
     for c in ctxs:
         c.sync()
 
+    # DRAM bytes per launch of the fused kernel (dram__bytes_read.sum +
+    # dram__bytes_write.sum) from one ncu capture of this workload in this
+    # launch shape; reported only when the run uses that shape
+    traffic = None
+    if (B, cluster, th_req) in PROFILED_SHAPES and prec == opo.OPO_FP32_PH64:
+        traffic = PROFILED_SHAPES[(B, cluster, th_req)]
     flops_rt = flops_per_roundtrip(base)
     achieved = flops_rt * B / (statistics.median(step_ms) * 1e-3) / 1e12
     peak = SMS * FP32_LANES * 2 * PEAK_SM_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "note": "FP32 vector peak from 152 SMs x 128 lanes x 2 x 2070 MHz; achieved = "
                         "algorithmic FLOPs of the batch round trip / median step time "
                         "(the fused kernel plus one finalize launch)"}
