@@ -118,11 +118,15 @@ void orc_kappa(const orc_params *p, double kappa_out[3])
 /* ----------------------------------------------------- linear operator --- */
 
 /* D_x(Omega) = exp{ dz [ -alpha/2 + i(-dbeta1 Omega + beta2 Omega^2/2
- *                                     - beta3 Omega^3/tod_div) ] }        */
+ *                                     - beta3 Omega^3/tod_div
+ *                                     + beta4 Omega^4/24) ] }
+ * (Taylor series of the propagation constant: with d/dtau <-> +i Omega the
+ * term of order k carries i (-1)^k beta_k Omega^k / k!)                   */
 static double complex dispersion_factor(const orc_params *p, int x, double om, double dz)
 {
     double phase = -p->dbeta1[x] * om + p->beta2[x] * om * om / 2.0
-                   - p->beta3[x] * om * om * om / p->tod_div;
+                   - p->beta3[x] * om * om * om / p->tod_div
+                   + p->beta4[x] * om * om * om * om / 24.0;
     double amp = exp(-p->alpha[x] * dz / 2.0);
     return amp * (cos(phase * dz) + I * sin(phase * dz));
 }
@@ -155,6 +159,21 @@ static void nl_rhs(const orc_params *p, const double kap[3], const double comple
         f[0] = I * (kap[0] / 2.0) * A[1] * A[1] * conj(e);
         f[1] = I * kap[1] * A[0] * conj(A[1]) * e;
     }
+    if (p->n2 != 0.0) {
+        /* Kerr: intensity-dependent index n2 I; a co-propagating field at
+         * another frequency counts twice (cross-phase modulation) */
+        double inten[3];
+        for (int x = 0; x < p->nfields; x++)
+            inten[x] = 0.5 * p->nidx[x] * EPS0 * C0 * creal(A[x] * conj(A[x]));
+        for (int x = 0; x < p->nfields; x++) {
+            double itot = inten[x];
+            for (int y = 0; y < p->nfields; y++)
+                if (y != x)
+                    itot += 2.0 * inten[y];
+            double k0 = 2.0 * ORC_PI / p->lambda[x];
+            f[x] += I * k0 * p->n2 * itot * A[x];
+        }
+    }
 }
 
 void orc_rk4_step(const orc_params *p, double *fields, double z0, double h)
@@ -167,7 +186,7 @@ void orc_rk4_step(const orc_params *p, double *fields, double z0, double h)
     for (int x = 0; x < F; x++)
         A[x] = (double complex *)(fields + (size_t)2 * n * x);
     for (int32_t j = 0; j < n; j++) {
-        double complex y[3], t[3], k1[3], k2[3], k3[3], k4[3];
+        double complex y[3] = {0}, t[3] = {0}, k1[3], k2[3], k3[3], k4[3];
         for (int x = 0; x < F; x++)
             y[x] = A[x][j];
         nl_rhs(p, kap, y, z0, k1);

@@ -61,6 +61,10 @@ typedef struct {
     double  ns_a0;          /* peak field amplitude [V/m]                         */
     double  ns_fwhm;        /* intensity FWHM [s]                                 */
     double  ns_t0;          /* pulse centre on the round-trip time axis [s]       */
+    /* chi(3) and higher-order dispersion (named as extensions in Sec. 1 and
+     * Sec. 2.1): fourth-order dispersion and the Kerr index */
+    double  beta4[3];       /* fourth derivative of k_x [s^4/m]                   */
+    double  n2;             /* Kerr index [m^2/W]; 0: no chi(3) terms             */
 } orc_params;
 
 /* In-place DFT of length n (power of two).  dir = -1: forward, unnormalized,
@@ -74,10 +78,15 @@ void orc_kappa(const orc_params *p, double kappa_out[3]);
 /* Angular frequency offset of bin k in FFT order: 2 pi k'/T. */
 double orc_omega(const orc_params *p, int32_t k);
 
-/* Linear step over dz on every field: A <- F^-1[ D(Omega) F[A] ]. */
+/* Linear step over dz on every field: A <- F^-1[ D(Omega) F[A] ], with
+ * D = exp{dz [-alpha/2 + i(-dbeta1 W + beta2 W^2/2 - beta3 W^3/tod_div
+ *                          + beta4 W^4/24)]}. */
 void orc_linear_step(const orc_params *p, double *fields, double dz);
 
-/* One classic RK4 step of size h from z0 on the pointwise nonlinear system. */
+/* One classic RK4 step of size h from z0 on the pointwise nonlinear system:
+ * the chi(2) terms of Eqs. (CEp)-(CEi) plus, when n2 != 0, self- and
+ * cross-phase modulation i k0_x n2 (I_x + 2 sum_{y != x} I_y) A_x with
+ * I_y = n_y eps0 c |A_y|^2 / 2 and k0_x = 2 pi / lambda_x. */
 void orc_rk4_step(const orc_params *p, double *fields, double z0, double h);
 
 /* One crystal pass: nz symmetrized steps N/2 - L - N/2. */

@@ -47,6 +47,8 @@ class Params(ctypes.Structure):
         ("ns_a0", ctypes.c_double),
         ("ns_fwhm", ctypes.c_double),
         ("ns_t0", ctypes.c_double),
+        ("beta4", ctypes.c_double * 3),
+        ("n2", ctypes.c_double),
     ]
 
 
@@ -103,6 +105,8 @@ def params(cfg, tod_div=6.0):
     p.dbeta1 = _trip(g("dbeta1", (0, 0, 0)))
     p.beta2 = _trip(g("beta2", (0, 0, 0)))
     p.beta3 = _trip(g("beta3", (0, 0, 0)))
+    p.beta4 = _trip(g("beta4", (0, 0, 0)))
+    p.n2 = float(g("n2"))
     p.tod_div = float(tod_div)
     p.w0 = float(g("w0", 55e-6))
     p.resonant_mask = int(cfg.resonant_mask)

@@ -79,6 +79,8 @@ class OPOConfig:
     dbeta1: tuple = (0.0, 0.0, 0.0)
     beta2: tuple = (0.0, 0.0, 0.0)
     beta3: tuple = (0.0, 0.0, 0.0)
+    beta4: tuple = (0.0, 0.0, 0.0)
+    n2: float = 0.0
     w0: float = 55e-6
     resonant_mask: int = 0b010
     R: tuple = (0.0, 0.98, 0.0)

@@ -39,6 +39,11 @@ MUTANTS = [
     ("ns pulse field FWHM", "exp(-2.0 * log(2.0) * t * t", "exp(-4.0 * log(2.0) * t * t"),
     ("ns slice ignores round trip", "double t = (double)m * p->t_rt + tau_of(p, j)",
      "double t = 0.0 * (double)m * p->t_rt + tau_of(p, j)"),
+    ("beta4 factor 1/12", "om * om * om * om / 24.0", "om * om * om * om / 12.0"),
+    ("beta4 sign", "+ p->beta4[x] * om", "- p->beta4[x] * om"),
+    ("XPM counted once", "itot += 2.0 * inten[y];", "itot += 1.0 * inten[y];"),
+    ("Kerr k0 of the signal", "double k0 = 2.0 * ORC_PI / p->lambda[x];",
+     "double k0 = 2.0 * ORC_PI / p->lambda[1];"),
 ]
 
 

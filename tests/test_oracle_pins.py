@@ -402,6 +402,103 @@ def test_power_and_centroid(orc):
     assert abs(orc.power(p, 2, a) - ref) <= 1e-14 * ref
 
 
+# --------------------------- fourth-order dispersion and Kerr (chi(3)) terms
+
+def test_beta4_matches_time_domain_fourth_derivative(orc):
+    """Fourth-order dispersion in the time domain is dA/dz = i (beta4/24)
+    d^4A/dtau^4 (convention-free).  For a Gaussian the fourth derivative is
+    (tau^4/T0^8 - 6 tau^2/T0^6 + 3/T0^4) A (Hermite closed form); a short step
+    must change A by dz times that, so sign and 1/24 are pinned."""
+    n, T = 1024, 20e-12
+    t = (np.arange(n) - n / 2) * (T / n)
+    T0 = 0.4e-12
+    A = np.exp(-t ** 2 / (2 * T0 ** 2)).astype(complex)
+    b4 = 1e-52
+    cfg = cw(n=n, t_window=T, beta4=(b4, 0.0, 0.0))
+    p = orc.params(cfg)
+    dz = 1e-6
+    out = orc.linear_step(p, np.stack([A, np.zeros(n), np.zeros(n)]), dz)[0]
+    d4 = (t ** 4 / T0 ** 8 - 6 * t ** 2 / T0 ** 6 + 3 / T0 ** 4) * A
+    ref = 1j * b4 / 24 * d4
+    got = (out - A) / dz
+    assert rel_l2(got, ref) <= 1e-4
+
+
+def test_beta4_single_mode_is_a_pure_phase(orc):
+    """A single Fourier mode is an eigenfunction of every dispersion order:
+    only its phase changes, by the same amount for bins +k and -k (even
+    order), and the power is unchanged."""
+    n = 64
+    cfg = cw(n=n, beta4=(0.0, 3e-52, 0.0))
+    p = orc.params(cfg)
+    j = np.arange(n)
+    for k in (3, 7):
+        a = np.stack([np.zeros(n), np.exp(2j * np.pi * k * j / n), np.zeros(n)])
+        b = np.stack([np.zeros(n), np.exp(-2j * np.pi * k * j / n), np.zeros(n)])
+        oa = orc.linear_step(p, a, 1e-3)[1]
+        ob = orc.linear_step(p, b, 1e-3)[1]
+        ra = oa / a[1]
+        rb = ob / b[1]
+        assert np.max(np.abs(np.abs(ra) - 1)) <= 1e-13
+        assert np.max(np.abs(ra - ra[0])) <= 1e-12
+        assert abs(ra[0] - rb[0]) <= 1e-12
+
+
+def _kerr_cfg(n2, **kw):
+    base = dict(n=4, nz=100, length=5e-3, deff=0.0, n2=n2)
+    base.update(kw)
+    return W.OPOConfig(**base)
+
+
+def test_kerr_self_phase_modulation_cw(orc):
+    """One CW field with intensity I in a Kerr medium: |A| is unchanged and the
+    phase grows by (2 pi / lambda) n2 I L (the nonlinear index n2 I)."""
+    n2 = 3e-17
+    cfg = _kerr_cfg(n2)
+    p = orc.params(cfg)
+    a0 = 2.0e7
+    A = np.stack([np.full(4, a0 + 0j), np.zeros(4, complex), np.zeros(4, complex)])
+    out = orc.crystal_pass(p, A)
+    inten = 0.5 * cfg.nidx[0] * EPS0 * C0 * a0 ** 2
+    phi = 2 * math.pi / cfg.lam[0] * n2 * inten * cfg.length
+    assert 0.05 < phi < 2.0
+    assert np.max(np.abs(out[0] - a0 * np.exp(1j * phi))) <= 1e-10 * a0
+
+
+def test_kerr_cross_phase_modulation_counts_twice(orc):
+    """Two CW fields at different wavelengths: each turns by
+    (2 pi / lambda_x) n2 (I_x + 2 I_y) L."""
+    n2 = 1e-17
+    cfg = _kerr_cfg(n2)
+    p = orc.params(cfg)
+    ap, as_ = 1.5e7, 2.5e7
+    A = np.stack([np.full(4, ap + 0j), np.full(4, as_ * 1j), np.zeros(4, complex)])
+    out = orc.crystal_pass(p, A)
+    Ip = 0.5 * cfg.nidx[0] * EPS0 * C0 * ap ** 2
+    Is = 0.5 * cfg.nidx[1] * EPS0 * C0 * as_ ** 2
+    php = 2 * math.pi / cfg.lam[0] * n2 * (Ip + 2 * Is) * cfg.length
+    phs = 2 * math.pi / cfg.lam[1] * n2 * (Is + 2 * Ip) * cfg.length
+    assert np.max(np.abs(out[0] - ap * np.exp(1j * php))) <= 1e-10 * ap
+    assert np.max(np.abs(out[1] - 1j * as_ * np.exp(1j * phs))) <= 1e-10 * as_
+    assert np.all(out[2] == 0)
+
+
+def test_kerr_keeps_chi2_exchange_and_total_power(orc):
+    """chi(2) + chi(3) together, no loss: the Kerr terms only rotate phases,
+    so sum_x n_x |A_x|^2 stays conserved to RK4 accuracy (error ~ dz^4)."""
+    cfg = W.OPOConfig(n=64, nz=100, length=10e-3, n2=3e-18)
+    p = orc.params(cfg)
+    rng = np.random.default_rng(5)
+    A = 4e6 * (rng.standard_normal((3, 64)) + 1j * rng.standard_normal((3, 64)))
+    out = orc.crystal_pass(p, A)
+    e0 = sum(cfg.nidx[x] * np.sum(np.abs(A[x]) ** 2) for x in range(3))
+    e1 = sum(cfg.nidx[x] * np.sum(np.abs(out[x]) ** 2) for x in range(3))
+    assert abs(e1 - e0) <= 1e-9 * e0
+    # and the result differs from the chi(2)-only pass
+    q = orc.params(cfg.replace(n2=0.0))
+    assert rel_l2(orc.crystal_pass(q, A), out) > 1e-3
+
+
 # ------------------------- ns-pulsed pump and pump-resonant (TRO) entry
 
 def _ns_cfg(n=64, **kw):
