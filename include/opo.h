@@ -33,6 +33,9 @@
  *                                    - beta3_x Omega^3/tod_div)]},
  *     with dbeta1_x = 1/nu_x - 1/nu_s (a slower field moves to later tau) and
  *     tod_div = 6 (Taylor; the paper prints 3, reachable through tod_div);
+ *   - fourth-order dispersion adds i beta4_x Omega^4/24 to the exponent of
+ *     D_x; a Kerr index n2 adds self- and cross-phase modulation (cross
+ *     terms counted twice) to the nonlinear step;
  *   - two-field (degenerate) mode: dA_p/dz = i (kappa_p/2) A_s^2 e^{-i dk z},
  *     dA_s/dz = i kappa_s A_p A_s* e^{+i dk z};
  *   - kappa_x = 2 pi d_eff / (n_x lambda_x); power P = mean|A|^2 n eps0 c/2
@@ -119,6 +122,12 @@ typedef struct {
     double  beta3_s3_per_m[3];  /* TOD k'''                                        */
     double  w0_m;               /* beam waist for power <-> intensity, > 0         */
     double  tod_div;            /* divisor of the TOD term; 0 selects 6            */
+    /* extensions the paper names without equations (Sec. 1, Sec. 2.1):      */
+    double  beta4_s4_per_m[3];  /* fourth-order dispersion: i beta4 Omega^4/24 in
+                                   the exponent of D_x                              */
+    double  n2_m2_per_W;        /* Kerr index: dA_x/dz += i (2 pi/lambda_x) n2
+                                   (I_x + 2 sum_{y != x} I_y) A_x, I_y =
+                                   n_y eps0 c |A_y|^2 / 2; 0 = no chi(3) terms     */
 } opo_crystal;
 
 /* Cavity and pump (Sec. 2.1 Eq. (BC), Sec. 2.3, Sec. 4). */

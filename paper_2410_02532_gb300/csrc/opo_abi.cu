@@ -121,6 +121,7 @@ int derive(opo_ctx *c)
     d.h = 0.5 * d.dz;
     d.use_dk = k.dk_per_m != 0.0;
     d.eom = v.eom_beta_rad != 0.0;
+    d.kerr = kerr_coefficients(k, c->F, d.kerr_g);
     d.ns = NsPump{};
     d.ns.n = c->n;
     d.ns.dt = c->grid.t_window_s / (double)c->n;
@@ -216,7 +217,8 @@ bool valid_crystal(const opo_ctx *c, const opo_crystal *k)
         return false;
     if (!finite_all(k->lambda_m, 3) || !finite_all(k->n, 3) || !finite_all(k->alpha_per_m, 3) ||
         !finite_all(k->dbeta1_s_per_m, 3) || !finite_all(k->beta2_s2_per_m, 3) ||
-        !finite_all(k->beta3_s3_per_m, 3))
+        !finite_all(k->beta3_s3_per_m, 3) || !finite_all(k->beta4_s4_per_m, 3) ||
+        !std::isfinite(k->n2_m2_per_W))
         return false;
     for (int x = 0; x < c->F; x++)
         if (!(k->lambda_m[x] > 0.0) || !(k->n[x] > 0.0))
@@ -256,7 +258,7 @@ int choose_path(opo_ctx *c, FusedCfg *cfg)
     if (c->path_req == OPO_PATH_PLAIN)
         return OPO_PATH_PLAIN;
     bool ok = fused_config(c->csz, c->F, c->F, c->n, c->n, c->cluster_req, c->rtpl_req,
-                           c->threads_req, cfg);
+                           c->threads_req, c->dv.kerr, cfg);
     if (c->path_req == OPO_PATH_FUSED)
         return ok ? OPO_PATH_FUSED : -1;
     return ok ? OPO_PATH_FUSED : OPO_PATH_PLAIN;
@@ -540,7 +542,8 @@ int opo_set_path(opo_ctx *c, int32_t path, int32_t cluster, int32_t rt_per_launc
     if (path == OPO_PATH_FUSED) {
         FusedCfg cfg;
         DeviceGuard g(c->device);
-        if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, rt_per_launch, threads, &cfg))
+        if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, rt_per_launch, threads,
+                          c->dv.kerr, &cfg))
             return OPO_E_UNSUPPORTED;
     }
     c->path_req = path;
@@ -636,7 +639,7 @@ int opo_fused_capacity(const opo_ctx *c, int32_t cluster, int32_t threads, int32
     if (!g.ok)
         return OPO_E_CUDA;
     FusedCfg cfg;
-    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, threads, &cfg))
+    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, threads, c->dv.kerr, &cfg))
         return OPO_E_UNSUPPORTED;
     *max_active = fused_max_active(c->prec == OPO_FP64, c->F, c->n, cfg);
     if (cluster_out)
@@ -740,13 +743,15 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
             const opo_ctx *g0 = b->groups[k].ctxs[0];
             int cl0, th0, rt0;
             want(g0, &cl0, &th0, &rt0);
-            if (g0->n == c->n && g0->F == c->F && cl0 == cl && th0 == th && rt0 == rt)
+            if (g0->n == c->n && g0->F == c->F && g0->dv.kerr == c->dv.kerr && cl0 == cl &&
+                th0 == th && rt0 == rt)
                 gi = (int)k;
         }
         if (gi < 0) {
             b->groups.emplace_back();
             gi = (int)b->groups.size() - 1;
-            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, &b->groups[gi].cfg)) {
+            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, c->dv.kerr,
+                              &b->groups[gi].cfg)) {
                 batch_free(b);
                 return OPO_E_UNSUPPORTED;
             }

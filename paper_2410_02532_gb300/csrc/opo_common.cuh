@@ -207,6 +207,60 @@ __device__ __forceinline__ void rk4_point(V *y, V e0, V e1, V e2,
     }
 }
 
+// RK4 step of the same system with the Kerr (chi(3)) terms added:
+//   dA_x/dz = i (c_x p_x + g_x A_x),  g_x = sum_y G_xy |A_y|^2,
+// where G_xy = (2 pi/lambda_x) n2 n_y eps0 c/2 times 1 (y = x) or 2 (y != x)
+// gives self- and cross-phase modulation.  G is row-major 3 x 3.
+template <int F, class V>
+__device__ __forceinline__ void rk4_point_kerr(V *y, V e0, V e1, V e2,
+                                               const typename cscal<V>::type *kap,
+                                               typename cscal<V>::type h, bool use_e,
+                                               const typename cscal<V>::type *G)
+{
+    using S = typename cscal<V>::type;
+    S c[F];
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        c[x] = (F == 2 && x == 0) ? kap[0] * (S)0.5 : kap[x];
+    auto rhs = [&](const V *a, V e, V *q) {
+        V p[F];
+        nl_prod<F>(a, e, use_e, p);
+        S i2[F];
+#pragma unroll
+        for (int x = 0; x < F; x++)
+            i2[x] = cabs2(a[x]);
+#pragma unroll
+        for (int x = 0; x < F; x++) {
+            S g = (S)0;
+#pragma unroll
+            for (int z = 0; z < F; z++)
+                g += G[3 * x + z] * i2[z];
+            q[x] = cmk<V>(c[x] * p[x].x + g * a[x].x, c[x] * p[x].y + g * a[x].y);
+        }
+    };
+    const S hh = h * (S)0.5, h6 = h / (S)6;
+    V q1[F], q2[F], q3[F], q4[F], t[F];
+    rhs(y, e0, q1);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = add_ig(y[x], hh, q1[x]);
+    rhs(t, e1, q2);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = add_ig(y[x], hh, q2[x]);
+    rhs(t, e1, q3);
+#pragma unroll
+    for (int x = 0; x < F; x++)
+        t[x] = add_ig(y[x], h, q3[x]);
+    rhs(t, e2, q4);
+#pragma unroll
+    for (int x = 0; x < F; x++) {
+        S sx = q1[x].x + (S)2 * q2[x].x + (S)2 * q3[x].x + q4[x].x;
+        S sy = q1[x].y + (S)2 * q2[x].y + (S)2 * q3[x].y + q4[x].y;
+        y[x] = add_ig(y[x], h6, cmk<V>(sx, sy));
+    }
+}
+
 // --------------------------------------------------- shared context ----
 // Slots of the raw per-round-trip observable sums (FP64): Sum|A_x|^2 for
 // x = 0..2, Sum_k |X_k|^2 and Sum_k k'|X_k|^2 of the signal spectrum.

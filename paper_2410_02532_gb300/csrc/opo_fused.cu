@@ -106,6 +106,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     const T kap[3] = {(T)d.kappa[0], (T)d.kappa[1], (T)d.kappa[2]};
     const T h = (T)d.h;
     const bool use_e = d.use_dk != 0;
+    const bool kerr = d.kerr != 0;
+    T kg[9];
+    for (int i = 0; i < 9; i++)
+        kg[i] = (T)d.kerr_g[i];
     const V *ekz = (const V *)d.ekz;
     const V *gG = (const V *)d.gdd;
     const V *gPump = (const V *)d.pump;
@@ -248,10 +252,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             y[2] = cmk<V>((T)0, (T)0);
             for (int f = 0; f < F; f++)
                 y[f] = src[f * NC + p];
-            if (F == 3)
+            if (kerr) {
+                if (F == 3)
+                    rk4_point_kerr<3>(y, e0, e1, e2, kap, h, use_e, kg);
+                else
+                    rk4_point_kerr<2>(y, e0, e1, e2, kap, h, use_e, kg);
+            } else if (F == 3) {
                 rk4_point<3>(y, e0, e1, e2, kap, h, use_e);
-            else
+            } else {
                 rk4_point<2>(y, e0, e1, e2, kap, h, use_e);
+            }
             for (int f = 0; f < F; f++)
                 X[f * NC + p] = y[f];
         }
@@ -390,7 +400,7 @@ bool cluster_launchable(bool dbl, int C, size_t sm)
 } // namespace
 
 bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluster_req,
-                  int rtpl_req, int threads_req, FusedCfg *out)
+                  int rtpl_req, int threads_req, bool kerr, FusedCfg *out)
 {
     const bool dbl = csz == sizeof(double2);
     const int lognmin = ilog2((unsigned)nmin), lognmax = ilog2((unsigned)nmax);
@@ -408,7 +418,7 @@ bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluste
         for (int i = 0; i < no; i++) {
             if (cluster_req > 0 && order[i] != cluster_req)
                 continue;
-            if (fused2_config(dbl, fmax, lognmax, order[i], threads_req, out)) {
+            if (fused2_config(dbl, kerr, fmax, lognmax, order[i], threads_req, out)) {
                 out->rt_per_launch = rtpl_req > 0 ? rtpl_req : 64;
                 return true;
             }
@@ -438,6 +448,7 @@ bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluste
             if (!cluster_launchable(dbl, C, sm))
                 break;
             best.kernel = 1;
+            best.kerr = kerr; // the generic kernel branches on it at run time
             best.cluster = C;
             best.threads = kFusedThreads;
             best.rt_per_launch = rtpl_req > 0 ? rtpl_req : 64;
@@ -499,6 +510,9 @@ void fill_desc(InstDesc &d, const opo_ctx *c)
     d.t_window = c->grid.t_window_s;
     d.m_start = c->rt;
     d.ns = c->dv.ns;
+    d.kerr = c->dv.kerr;
+    for (int i = 0; i < 9; i++)
+        d.kerr_g[i] = c->dv.kerr_g[i];
 }
 
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s)

@@ -7,18 +7,23 @@
 namespace opo {
 namespace {
 
-int dispatch(int op, bool ip, bool dbl, int F, int logn, const InstDesc *dd, int count, int C,
-             int threads, size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
+int dispatch(int op, bool ip, bool kr, bool dbl, int F, int logn, const InstDesc *dd, int count,
+             int C, int threads, size_t sm, bool ds, int r_base, int chunk, int last,
+             cudaStream_t s)
 {
     if (dbl)
-        return F == 3 ? f2::dispatch_f64_f3(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s)
-                      : f2::dispatch_f64_f2(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
-    return F == 3 ? f2::dispatch_f32_f3(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s)
-                  : f2::dispatch_f32_f2(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
+        return F == 3 ? f2::dispatch_f64_f3(op, ip, kr, logn, dd, count, C, threads, sm, ds, r_base,
+                                            chunk, last, s)
+                      : f2::dispatch_f64_f2(op, ip, kr, logn, dd, count, C, threads, sm, ds, r_base,
+                                            chunk, last, s);
+    return F == 3 ? f2::dispatch_f32_f3(op, ip, kr, logn, dd, count, C, threads, sm, ds, r_base,
+                                        chunk, last, s)
+                  : f2::dispatch_f32_f2(op, ip, kr, logn, dd, count, C, threads, sm, ds, r_base,
+                                        chunk, last, s);
 }
 
 // In-place variant: X and Y only, dispersion factors from L2.
-bool ip_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
+bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
     if (logn != 14 && logn != 15)
         return false;
@@ -41,13 +46,14 @@ bool ip_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
     size_t sm = el * csz + 32 * kNslot * sizeof(double);
     if (sm > 227 * 1024)
         return false;
-    if (dispatch(1, true, dbl, F, logn, nullptr, 0, C, threads, sm, false, 0, 0, 0, nullptr) < 1)
+    if (dispatch(1, true, kr, dbl, F, logn, nullptr, 0, C, threads, sm, false, 0, 0, 0, nullptr) < 1)
         return false;
     out->cluster = C;
     out->threads = threads;
     out->disp_in_smem = false;
     out->smem = sm;
     out->kernel = 3;
+    out->kerr = kr;
     return true;
 }
 
@@ -55,7 +61,8 @@ bool ip_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
 
 namespace {
 
-bool three_buffer_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
+bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_req,
+                         FusedCfg *out)
 {
     const int LP = logn / 2, LQ = logn - LP;
     if ((1 << LP) < C || (1 << LQ) < C)
@@ -81,13 +88,15 @@ bool three_buffer_config(bool dbl, int F, int logn, int C, int threads_req, Fuse
         size_t sm = el * csz + 32 * kNslot * sizeof(double);
         if (sm > 227 * 1024)
             continue;
-        if (dispatch(1, false, dbl, F, logn, nullptr, 0, C, threads, sm, ds == 1, 0, 0, 0, nullptr) < 1)
+        if (dispatch(1, false, kr, dbl, F, logn, nullptr, 0, C, threads, sm, ds == 1, 0, 0, 0,
+                     nullptr) < 1)
             continue;
         out->cluster = C;
         out->threads = threads;
         out->disp_in_smem = ds == 1;
         out->smem = sm;
         out->kernel = 2;
+        out->kerr = kr;
         return true;
     }
     return false;
@@ -100,13 +109,13 @@ bool three_buffer_config(bool dbl, int F, int logn, int C, int threads_req, Fuse
 // points per CTA, so where both fit it usually packs two CTAs per SM); on a
 // tie the three-buffer form, which keeps the dispersion factors in shared
 // memory.
-bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out)
+bool fused2_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
     if (logn < 12 || logn > 15)
         return false;
     FusedCfg a, b;
-    const bool ok_a = three_buffer_config(dbl, F, logn, C, threads_req, &a);
-    const bool ok_b = ip_config(dbl, F, logn, C, threads_req, &b);
+    const bool ok_a = three_buffer_config(dbl, kr, F, logn, C, threads_req, &a);
+    const bool ok_b = ip_config(dbl, kr, F, logn, C, threads_req, &b);
     if (!ok_a && !ok_b)
         return false;
     if (ok_a && ok_b) {
@@ -121,15 +130,15 @@ bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *
 
 int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg)
 {
-    return dispatch(1, cfg.kernel == 3, dbl, F, logn, nullptr, 0, cfg.cluster, cfg.threads,
-                    cfg.smem, cfg.disp_in_smem, 0, 0, 0, nullptr);
+    return dispatch(1, cfg.kernel == 3, cfg.kerr, dbl, F, logn, nullptr, 0, cfg.cluster,
+                    cfg.threads, cfg.smem, cfg.disp_in_smem, 0, 0, 0, nullptr);
 }
 
 int fused2_launch(bool dbl, int F, int logn, const InstDesc *dd, int count, const FusedCfg &cfg,
                   int r_base, int chunk, int last, cudaStream_t s)
 {
-    return dispatch(0, cfg.kernel == 3, dbl, F, logn, dd, count, cfg.cluster, cfg.threads,
-                    cfg.smem, cfg.disp_in_smem, r_base, chunk, last, s);
+    return dispatch(0, cfg.kernel == 3, cfg.kerr, dbl, F, logn, dd, count, cfg.cluster,
+                    cfg.threads, cfg.smem, cfg.disp_in_smem, r_base, chunk, last, s);
 }
 
 } // namespace opo

@@ -72,7 +72,9 @@ __device__ __forceinline__ void dft_r(V *v)
 template <class T, bool IP>
 constexpr int kF2MaxThreads = IP ? F2IpTraits<T>::kMaxThreads : F2Traits<T>::kMaxThreads;
 
-template <class T, int F, int LP, int LQ, bool IP>
+// KR: the Kerr (chi(3)) terms are part of the nonlinear step (a separate
+// instantiation, so that the chi(2)-only kernel keeps its registers and code)
+template <class T, int F, int LP, int LQ, bool IP, bool KR>
 __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     k_fused2(const InstDesc *__restrict__ descs, int r_base, int M, int write_out, int disp_smem)
 {
@@ -112,6 +114,10 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     const int nz = dg.nz;
     const bool use_e = dg.use_dk != 0;
     const bool eom = dg.eom != 0;
+    constexpr bool kerr = KR;
+    __shared__ T sG[KR ? 9 : 1]; // Kerr coefficients G_xy
+    if (KR && threadIdx.x < 9)
+        sG[threadIdx.x] = (T)dg.kerr_g[threadIdx.x];
     const T kap[3] = {(T)dg.kappa[0], (T)dg.kappa[1], (T)dg.kappa[2]};
     const T h = (T)dg.h;
     V bc[3], osc[3];
@@ -254,7 +260,10 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
 #pragma unroll
                     for (int f = 0; f < F; f++)
                         y[f] = v[f][r];
-                    rk4_point<F>(y, e0a, e1a, e2a, kap, h, use_e);
+                    if constexpr (kerr)
+                        rk4_point_kerr<F>(y, e0a, e1a, e2a, kap, h, use_e, sG);
+                    else
+                        rk4_point<F>(y, e0a, e1a, e2a, kap, h, use_e);
 #pragma unroll
                     for (int f = 0; f < F; f++)
                         v[f][r] = y[f];
@@ -325,7 +334,10 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                     for (int f = 1; f < F; f++)
                         if (!(resmask & (1u << f)))
                             y[f] = cmk<V>((T)0, (T)0);
-                    rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
+                    if constexpr (kerr)
+                        rk4_point_kerr<F>(y, e0b, e1b, e2b, kap, h, use_e, sG);
+                    else
+                        rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
 #pragma unroll
                     for (int f = 0; f < F; f++)
                         v[f][r] = y[f];
@@ -337,7 +349,10 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
 #pragma unroll
                     for (int f = 0; f < F; f++)
                         y[f] = v[f][r];
-                    rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
+                    if constexpr (kerr)
+                        rk4_point_kerr<F>(y, e0b, e1b, e2b, kap, h, use_e, sG);
+                    else
+                        rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
 #pragma unroll
                     for (int f = 0; f < F; f++)
                         v[f][r] = y[f];
@@ -681,11 +696,11 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     }
 }
 
-template <class T, int F, int LP, int LQ, bool IP>
+template <class T, int F, int LP, int LQ, bool IP, bool KR>
 int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool disp_smem,
              int r_base, int chunk, int last, cudaStream_t s)
 {
-    auto kern = k_fused2<T, F, LP, LQ, IP>;
+    auto kern = k_fused2<T, F, LP, LQ, IP, KR>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t lc = {};
@@ -704,10 +719,10 @@ int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool 
     return e == cudaSuccess ? OPO_OK : OPO_E_CUDA;
 }
 
-template <class T, int F, int LP, int LQ, bool IP>
+template <class T, int F, int LP, int LQ, bool IP, bool KR>
 int max_active_t(int C, int threads, size_t sm)
 {
-    auto kern = k_fused2<T, F, LP, LQ, IP>;
+    auto kern = k_fused2<T, F, LP, LQ, IP, KR>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t lc = {};
@@ -731,45 +746,69 @@ int max_active_t(int C, int threads, size_t sm)
 
 // Launch (op 0) or occupancy query (op 1) of every instantiated size for one
 // precision and field count; ip selects the in-place variant (2^14 and 2^15
-// only).  Defined by the opo_fused2_*.cu units.
+// only), kr the instantiation with the Kerr terms.  The chi(2)-only and the
+// Kerr instantiations of a precision and field count are defined in two
+// translation units (opo_fused2_<prec>_<F>.cu and ..._kerr.cu) that compile in
+// parallel.
 #define OPO_F2_DISPATCH_DECL(NAME)                                                               \
+    int NAME(int op, bool ip, bool kr, int logn, const InstDesc *dd, int count, int C,          \
+             int threads, size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
+#define OPO_F2_DISPATCH_KR_DECL(NAME)                                                            \
     int NAME(int op, bool ip, int logn, const InstDesc *dd, int count, int C, int threads,      \
              size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
 OPO_F2_DISPATCH_DECL(dispatch_f32_f3);
 OPO_F2_DISPATCH_DECL(dispatch_f32_f2);
 OPO_F2_DISPATCH_DECL(dispatch_f64_f3);
 OPO_F2_DISPATCH_DECL(dispatch_f64_f2);
+OPO_F2_DISPATCH_KR_DECL(dispatch_f32_f3_kerr);
+OPO_F2_DISPATCH_KR_DECL(dispatch_f32_f2_kerr);
+OPO_F2_DISPATCH_KR_DECL(dispatch_f64_f3_kerr);
+OPO_F2_DISPATCH_KR_DECL(dispatch_f64_f2_kerr);
 
-#define OPO_F2_ONE(T, F, LP, LQ, IP)                                                             \
-    return op == 0 ? launch_t<T, F, LP, LQ, IP>(dd, count, C, threads, sm, ds, r_base, chunk,   \
-                                                last, s)                                         \
-                   : max_active_t<T, F, LP, LQ, IP>(C, threads, sm)
+#define OPO_F2_ONE(T, F, LP, LQ, IP, KR)                                                         \
+    return op == 0 ? launch_t<T, F, LP, LQ, IP, KR>(dd, count, C, threads, sm, ds, r_base,      \
+                                                    chunk, last, s)                              \
+                   : max_active_t<T, F, LP, LQ, IP, KR>(C, threads, sm)
 
-#define OPO_F2_DISPATCH_DEF(NAME, T, F)                                                          \
-    OPO_F2_DISPATCH_DECL(NAME)                                                                   \
-    {                                                                                            \
-        if (ip) {                                                                                \
-            switch (logn) {                                                                      \
-            case 14:                                                                             \
-                OPO_F2_ONE(T, F, 7, 7, true);                                                    \
-            case 15:                                                                             \
-                OPO_F2_ONE(T, F, 7, 8, true);                                                    \
-            default:                                                                             \
-                return op == 0 ? OPO_E_UNSUPPORTED : 0;                                          \
-            }                                                                                    \
-        }                                                                                        \
+// every size for one (T, F, KR)
+#define OPO_F2_SIZES(T, F, KR)                                                                   \
+    if (ip) {                                                                                    \
         switch (logn) {                                                                          \
-        case 12:                                                                                 \
-            OPO_F2_ONE(T, F, 6, 6, false);                                                       \
-        case 13:                                                                                 \
-            OPO_F2_ONE(T, F, 6, 7, false);                                                       \
-        case 14:                                                                             \
-            OPO_F2_ONE(T, F, 7, 7, false);                                                       \
+        case 14:                                                                                 \
+            OPO_F2_ONE(T, F, 7, 7, true, KR);                                                    \
         case 15:                                                                                 \
-            OPO_F2_ONE(T, F, 7, 8, false);                                                       \
+            OPO_F2_ONE(T, F, 7, 8, true, KR);                                                    \
         default:                                                                                 \
             return op == 0 ? OPO_E_UNSUPPORTED : 0;                                              \
         }                                                                                        \
+    }                                                                                            \
+    switch (logn) {                                                                              \
+    case 12:                                                                                     \
+        OPO_F2_ONE(T, F, 6, 6, false, KR);                                                       \
+    case 13:                                                                                     \
+        OPO_F2_ONE(T, F, 6, 7, false, KR);                                                       \
+    case 14:                                                                                     \
+        OPO_F2_ONE(T, F, 7, 7, false, KR);                                                       \
+    case 15:                                                                                     \
+        OPO_F2_ONE(T, F, 7, 8, false, KR);                                                       \
+    default:                                                                                     \
+        return op == 0 ? OPO_E_UNSUPPORTED : 0;                                                  \
+    }
+
+// the chi(2)-only sizes, and the entry point that forwards Kerr requests
+#define OPO_F2_DISPATCH_DEF(NAME, T, F)                                                          \
+    OPO_F2_DISPATCH_DECL(NAME)                                                                   \
+    {                                                                                            \
+        if (kr)                                                                                  \
+            return NAME##_kerr(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk,      \
+                               last, s);                                                         \
+        OPO_F2_SIZES(T, F, false)                                                                \
+    }
+
+#define OPO_F2_DISPATCH_KERR_DEF(NAME, T, F)                                                     \
+    OPO_F2_DISPATCH_KR_DECL(NAME##_kerr)                                                         \
+    {                                                                                            \
+        OPO_F2_SIZES(T, F, true)                                                                 \
     }
 
 } // namespace f2

@@ -1,0 +1,9 @@
+// Instantiates the size-specialised fused kernel with the Kerr terms for
+// float fields, 3 fields.
+#include "opo_fused2.cuh"
+
+namespace opo {
+namespace f2 {
+OPO_F2_DISPATCH_KERR_DEF(dispatch_f32_f3, float, 3)
+} // namespace f2
+} // namespace opo

@@ -29,6 +29,8 @@ struct InstDesc {
     double pscale[3];  // n eps0 c / 2 * pi w0^2
     int64_t m_start;   // round-trip counter at the start of the call
     NsPump ns;         // ns-pulsed pump (ns.on), replaces the pump table
+    int kerr;          // chi(3) terms on
+    double kerr_g[9];  // their coefficients G_xy, row-major
 };
 
 // Observables of every instance and slot of the call: output power
@@ -82,7 +84,7 @@ void fill_desc(InstDesc &d, const opo_ctx *c);
 
 // opo_fused2.cu: the size-specialised kernel (N = 2^12 .. 2^15, one size and
 // field count per launch).
-bool fused2_config(bool dbl, int F, int logn, int C, int threads_req, FusedCfg *out);
+bool fused2_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out);
 int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg);
 int fused2_launch(bool dbl, int F, int logn, const InstDesc *dd, int count, const FusedCfg &cfg,
                   int r_base, int chunk, int last, cudaStream_t s);

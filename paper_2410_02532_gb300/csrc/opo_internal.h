@@ -34,11 +34,14 @@ struct Derived {
     double pscale[3];    // n eps0 c / 2 * pi w0^2
     bool use_dk;
     bool eom;
+    bool kerr;             // chi(3) terms on
+    double kerr_g[9];      // G_xy of the Kerr terms, row-major
     NsPump ns;           // ns-pulsed pump parameters (ns.on = 0: pump table)
 };
 
 struct FusedCfg {
     int kernel = 1;      // 1: generic, 2: size-specialised, 3: size-specialised in place
+    bool kerr = false;   // instances carry the chi(3) terms (kernels 2, 3 instantiate it)
     int cluster;         // CTAs per instance
     int threads;         // threads per CTA
     int rt_per_launch;   // round trips per launch
@@ -108,13 +111,17 @@ void plain_prepare(opo_ctx *c);
 int plain_enqueue_roundtrip(opo_ctx *c, cudaStream_t s);
 // one crystal pass of the plain kernels on caller-given buffers
 int plain_pass_raw(void *fields, void *scratch, const void *tw, const void *disp, const void *ekz,
-                   int n, int F, int nz, const double kappa[3], double h, bool use_dk, bool dbl,
-                   cudaStream_t st);
+                   int n, int F, int nz, const double kappa[3], double h, bool use_dk,
+                   const double *kerr_g, bool dbl, cudaStream_t st);
+
+// opo_setup.cu: coefficients G_xy (row-major 3 x 3) of the Kerr terms of a
+// crystal; false (all zero) when its n2 is 0.
+bool kerr_coefficients(const opo_crystal &k, int F, double g[9]);
 
 // opo_fused.cu: a cluster configuration able to hold instances with up to
 // fmax fields and nmin..nmax points (false if none fits or can launch).
 bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluster_req,
-                  int rtpl_req, int threads_req, FusedCfg *out);
+                  int rtpl_req, int threads_req, bool kerr, FusedCfg *out);
 int fused_max_active(bool dbl, int F, int n, const FusedCfg &cfg);
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s);
 

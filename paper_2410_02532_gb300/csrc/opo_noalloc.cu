@@ -65,8 +65,10 @@ extern "C" OPO_API int opo_crystal_pass_noalloc(const opo_grid *grid, const opo_
         if (!(k->lambda_m[x] > 0.0) || !(k->n[x] > 0.0) || !std::isfinite(k->lambda_m[x]) ||
             !std::isfinite(k->n[x]) || !std::isfinite(k->alpha_per_m[x]) ||
             !std::isfinite(k->dbeta1_s_per_m[x]) || !std::isfinite(k->beta2_s2_per_m[x]) ||
-            !std::isfinite(k->beta3_s3_per_m[x]))
+            !std::isfinite(k->beta3_s3_per_m[x]) || !std::isfinite(k->beta4_s4_per_m[x]))
             return OPO_E_INVALID;
+    if (!std::isfinite(k->n2_m2_per_W))
+        return OPO_E_INVALID;
     const bool dbl = grid->precision == OPO_FP64;
     const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
     // scratch layout: twiddles N | FFT intermediate F*N | dispersion F*N | ekz 4 nz + 1
@@ -100,8 +102,10 @@ extern "C" OPO_API int opo_crystal_pass_noalloc(const opo_grid *grid, const opo_
             for (int x = 0; x < F; x++)
                 kappa[x] = 2.0 * opo::kPi * k->deff_mpv / (k->n[x] * k->lambda_m[x]);
             const double h = 0.5 * k->length_m / (double)k->nz;
+            double kg[9];
+            const bool kerr = opo::kerr_coefficients(*k, F, kg);
             rc = opo::plain_pass_raw(fields, scr, tw, disp, ekz, n, F, k->nz, kappa, h,
-                                     k->dk_per_m != 0.0, dbl, s);
+                                     k->dk_per_m != 0.0, kerr ? kg : nullptr, dbl, s);
         }
     }
     if (prev >= 0)

@@ -39,9 +39,23 @@ __global__ void k_entry(cv<T> *fields, const cv<T> *pump, int n, int F, unsigned
     }
 }
 
+// Kerr coefficients G_xy (row-major) in the field precision.
+template <class T> struct KerrG {
+    T g[9];
+};
+
+template <class T>
+KerrG<T> kerr_g(const double *g)
+{
+    KerrG<T> k;
+    for (int i = 0; i < 9; i++)
+        k.g[i] = (T)g[i];
+    return k;
+}
+
 template <class T, int F>
 __global__ void k_rk4(cv<T> *fields, int n, const cv<T> *ekz, int q0, T h, T k0, T k1, T k2,
-                      bool use_e)
+                      bool use_e, bool kerr, KerrG<T> G)
 {
     using V = cv<T>;
     const T kap[3] = {k0, k1, k2};
@@ -51,7 +65,10 @@ __global__ void k_rk4(cv<T> *fields, int n, const cv<T> *ekz, int q0, T h, T k0,
 #pragma unroll
         for (int x = 0; x < F; x++)
             y[x] = fields[(size_t)x * n + j];
-        rk4_point<F>(y, e0, e1, e2, kap, h, use_e);
+        if (kerr)
+            rk4_point_kerr<F>(y, e0, e1, e2, kap, h, use_e, G.g);
+        else
+            rk4_point<F>(y, e0, e1, e2, kap, h, use_e);
 #pragma unroll
         for (int x = 0; x < F; x++)
             fields[(size_t)x * n + j] = y[x];
@@ -330,10 +347,12 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
             int q0 = 4 * j + 2 * half;
             if (F == 3)
                 k_rk4<T, 3><<<gN, kThreads, 0, st>>>(fld, n, ekz, q0, h, (T)d.kappa[0],
-                                                     (T)d.kappa[1], (T)d.kappa[2], d.use_dk);
+                                                     (T)d.kappa[1], (T)d.kappa[2], d.use_dk,
+                                                     d.kerr, kerr_g<T>(d.kerr_g));
             else
                 k_rk4<T, 2><<<gN, kThreads, 0, st>>>(fld, n, ekz, q0, h, (T)d.kappa[0],
-                                                     (T)d.kappa[1], (T)d.kappa[2], d.use_dk);
+                                                     (T)d.kappa[1], (T)d.kappa[2], d.use_dk,
+                                                     d.kerr, kerr_g<T>(d.kerr_g));
             if (half == 0) {
                 fft.template run<-1>(fld, scr, F, st);
                 k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_disp, F * n);
@@ -410,8 +429,12 @@ namespace {
 // The crystal pass alone (nz symmetrized steps) on caller-provided buffers.
 template <class T>
 int pass_raw(void *fields, void *scratch, const void *tw, const void *disp, const void *ekz,
-             int n, int F, int nz, const double kappa[3], double h, bool use_dk, cudaStream_t st)
+             int n, int F, int nz, const double kappa[3], double h, bool use_dk,
+             const double *kg, cudaStream_t st)
 {
+    const double zero[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const bool kerr = kg != nullptr;
+    const KerrG<T> G = kerr_g<T>(kg ? kg : zero);
     using V = cv<T>;
     prepare<T>();
     V *fld = (V *)fields;
@@ -424,10 +447,10 @@ int pass_raw(void *fields, void *scratch, const void *tw, const void *disp, cons
             int q0 = 4 * j + 2 * half;
             if (F == 3)
                 k_rk4<T, 3><<<gN, kThreads, 0, st>>>(fld, n, (const V *)ekz, q0, (T)h, (T)kappa[0],
-                                                     (T)kappa[1], (T)kappa[2], use_dk);
+                                                     (T)kappa[1], (T)kappa[2], use_dk, kerr, G);
             else
                 k_rk4<T, 2><<<gN, kThreads, 0, st>>>(fld, n, (const V *)ekz, q0, (T)h, (T)kappa[0],
-                                                     (T)kappa[1], (T)kappa[2], use_dk);
+                                                     (T)kappa[1], (T)kappa[2], use_dk, kerr, G);
             if (half == 0) {
                 fft.template run<-1>(fld, scr, F, st);
                 k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)disp, F * n);
@@ -441,11 +464,13 @@ int pass_raw(void *fields, void *scratch, const void *tw, const void *disp, cons
 } // namespace
 
 int plain_pass_raw(void *fields, void *scratch, const void *tw, const void *disp, const void *ekz,
-                   int n, int F, int nz, const double kappa[3], double h, bool use_dk, bool dbl,
-                   cudaStream_t st)
+                   int n, int F, int nz, const double kappa[3], double h, bool use_dk,
+                   const double *kerr_g, bool dbl, cudaStream_t st)
 {
-    return dbl ? pass_raw<double>(fields, scratch, tw, disp, ekz, n, F, nz, kappa, h, use_dk, st)
-               : pass_raw<float>(fields, scratch, tw, disp, ekz, n, F, nz, kappa, h, use_dk, st);
+    return dbl ? pass_raw<double>(fields, scratch, tw, disp, ekz, n, F, nz, kappa, h, use_dk,
+                                  kerr_g, st)
+               : pass_raw<float>(fields, scratch, tw, disp, ekz, n, F, nz, kappa, h, use_dk,
+                                 kerr_g, st);
 }
 
 } // namespace opo

@@ -25,7 +25,7 @@ __global__ void k_twiddles(cv<T> *tw, int n)
 }
 
 struct DispArgs {
-    double alpha[3], db1[3], b2[3], b3[3];
+    double alpha[3], db1[3], b2[3], b3[3], b4[3];
     double tod_div, dz, t_window;
 };
 
@@ -51,7 +51,8 @@ __global__ void k_disp_table(cv<T> *D, cv<T> *Dt, int logP, int n, int F, DispAr
         int x = i / n, k = i % n;
         double om = omega_k(k, n, a.t_window);
         double ph = a.dz * (-a.db1[x] * om + a.b2[x] * om * om * 0.5
-                            - a.b3[x] * om * om * om / a.tod_div);
+                            - a.b3[x] * om * om * om / a.tod_div
+                            + a.b4[x] * om * om * om * om / 24.0);
         double amp = exp(-a.alpha[x] * a.dz * 0.5) * inv_n;
         double s, c;
         sincos(ph, &s, &c);
@@ -151,6 +152,20 @@ int setup_twiddles(opo_ctx *c)
     return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
 }
 
+// Kerr: dA_x/dz += i (sum_y G_xy |A_y|^2) A_x with
+// G_xy = (2 pi / lambda_x) n2 (n_y eps0 c / 2) (1 if y = x, else 2).
+bool kerr_coefficients(const opo_crystal &k, int F, double g[9])
+{
+    const bool on = k.n2_m2_per_W != 0.0;
+    for (int x = 0; x < 3; x++)
+        for (int y = 0; y < 3; y++)
+            g[3 * x + y] = (on && x < F && y < F)
+                               ? (2.0 * kPi / k.lambda_m[x]) * k.n2_m2_per_W *
+                                     (0.5 * k.n[y] * kEps0 * kC0) * (x == y ? 1.0 : 2.0)
+                               : 0.0;
+    return on;
+}
+
 int setup_crystal_tables(opo_ctx *c)
 {
     const opo_crystal &k = c->crystal;
@@ -160,6 +175,7 @@ int setup_crystal_tables(opo_ctx *c)
         a.db1[x] = k.dbeta1_s_per_m[x];
         a.b2[x] = k.beta2_s2_per_m[x];
         a.b3[x] = k.beta3_s3_per_m[x];
+        a.b4[x] = k.beta4_s4_per_m[x];
     }
     a.tod_div = k.tod_div > 0.0 ? k.tod_div : 6.0;
     a.dz = k.length_m / (double)k.nz;
@@ -217,6 +233,7 @@ int setup_pass_tables(void *tw, void *disp, void *ekz, int n, int F, bool dbl,
         a.db1[x] = k.dbeta1_s_per_m[x];
         a.b2[x] = k.beta2_s2_per_m[x];
         a.b3[x] = k.beta3_s3_per_m[x];
+        a.b4[x] = k.beta4_s4_per_m[x];
     }
     a.tod_div = k.tod_div > 0.0 ? k.tod_div : 6.0;
     a.dz = k.length_m / (double)k.nz;

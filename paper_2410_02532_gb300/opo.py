@@ -39,7 +39,8 @@ class Crystal(ctypes.Structure):
                 ("dk_per_m", ctypes.c_double), ("deff_mpv", ctypes.c_double),
                 ("lambda_m", _D3), ("n", _D3), ("alpha_per_m", _D3),
                 ("dbeta1_s_per_m", _D3), ("beta2_s2_per_m", _D3), ("beta3_s3_per_m", _D3),
-                ("w0_m", ctypes.c_double), ("tod_div", ctypes.c_double)]
+                ("w0_m", ctypes.c_double), ("tod_div", ctypes.c_double),
+                ("beta4_s4_per_m", _D3), ("n2_m2_per_W", ctypes.c_double)]
 
 
 class Cavity(ctypes.Structure):
@@ -240,6 +241,8 @@ def crystal_from(cfg, tod_div=0.0) -> Crystal:
     c.beta3_s3_per_m = _D3(*cfg.beta3)
     c.w0_m = cfg.w0
     c.tod_div = tod_div
+    c.beta4_s4_per_m = _D3(*getattr(cfg, "beta4", (0.0, 0.0, 0.0)))
+    c.n2_m2_per_W = getattr(cfg, "n2", 0.0)
     return c
 
 

@@ -240,3 +240,68 @@ def test_specialised_kernels(name, make, prec, cluster):
             assert abs(got[2][r, x] - ref[2][r, x]) <= 4 * tol * abs(ref[2][r, x]) + 1e-300
     if cluster:
         assert got[3].cluster == cluster
+
+
+# ------------------ chi(3) Kerr terms and fourth-order dispersion (every path)
+
+def cfg_kerr(n=1024, nz=10, F=3):
+    """chi(2) + Kerr (n2 large enough to turn the phase by ~0.1-1 rad per
+    pass at these fields) + fourth-order dispersion on top of GVM/GVD/TOD."""
+    if F == 3:
+        c = W.cw_sro_16k().replace(n=n, nz=nz, length=10e-3, dk=50.0, name="kerr3")
+    else:
+        c = W.degenerate_2field(n=n, level=3.0).replace(nz=nz, dk=80.0, name="kerr2")
+    return c.replace(n2=2e-17, beta4=(4e-55, -3e-55, 2e-55))
+
+
+KERR_CASES = {
+    "kerr_3field_1024": (lambda: cfg_kerr(1024, 10, 3), 0, opo.OPO_PATH_PLAIN),
+    "kerr_3field_1024_fused": (lambda: cfg_kerr(1024, 10, 3), 0, opo.OPO_PATH_FUSED),
+    "kerr_2field_512_fused": (lambda: cfg_kerr(512, 10, 2), 0, opo.OPO_PATH_FUSED),
+    "kerr_3field_4096": (lambda: cfg_kerr(4096, 6, 3), 0, opo.OPO_PATH_FUSED),
+    "kerr_2field_8192": (lambda: cfg_kerr(8192, 5, 2), 0, opo.OPO_PATH_FUSED),
+    "kerr_3field_16384_c4": (lambda: cfg_kerr(16384, 3, 3), 4, opo.OPO_PATH_FUSED),
+    "kerr_3field_16384_c8": (lambda: cfg_kerr(16384, 3, 3), 8, opo.OPO_PATH_FUSED),
+    "kerr_3field_32768_c8": (lambda: cfg_kerr(32768, 2, 3), 8, opo.OPO_PATH_FUSED),
+}
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=["fp64", "fp32ph64"])
+@pytest.mark.parametrize("case", sorted(KERR_CASES))
+def test_kerr_round_trip(case, prec):
+    make, cluster, path = KERR_CASES[case]
+    cfg = make()
+    a0 = start(cfg, amp=3e6)
+    ref = oracle_rt(cfg, a0, m0=2)
+    try:
+        got = gpu_rt(cfg, a0, prec, path, cluster=cluster, m0=2)
+    except opo.OPOError as e:  # FP64 at 2^15 does not fit these clusters
+        assert e.status == opo.OPO_E_UNSUPPORTED and prec == opo.OPO_FP64
+        return
+    check(cfg, got, ref, prec, case)
+    # the chi(3) terms matter at this size: without them the oracle differs
+    ref0 = oracle_rt(cfg.replace(n2=0.0, beta4=(0.0, 0.0, 0.0)), a0, m0=2)
+    assert rel_l2(ref0[0][1], ref[0][1]) > 100 * TOL[prec]
+
+
+def test_kerr_allocation_free_pass():
+    """The allocation-free crystal pass carries the chi(3) terms too."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    L = opo.lib()
+    L.opo_crystal_pass_noalloc.argtypes = [ctypes.POINTER(opo.Grid), ctypes.POINTER(opo.Crystal),
+                                           ctypes.c_void_p, ctypes.c_void_p]
+    L.opo_crystal_pass_noalloc.restype = ctypes.c_int
+    cfg = cfg_kerr(1024, 8, 3)
+    a0 = start(cfg, amp=3e6)
+    a0[0] = 2e6
+    ref = orc.crystal_pass(orc.params(cfg), a0)
+    dev = torch.tensor(a0, dtype=torch.complex128, device="cuda").contiguous()
+    st = L.opo_crystal_pass_noalloc(ctypes.byref(opo.grid_from(cfg, opo.OPO_FP64)),
+                                    ctypes.byref(opo.crystal_from(cfg)), dev.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+    assert st == opo.OPO_OK
+    torch.cuda.synchronize()
+    got = dev.cpu().numpy()
+    for x in range(cfg.nfields):
+        assert rel_l2(got[x], ref[x]) <= 1e-10
