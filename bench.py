@@ -65,7 +65,8 @@ def flops_per_roundtrip(cfg):
 
     per point-field per z-step: two FFTs 2 * 5 log2 N, dispersion multiply 6,
     two RK4 half steps 2 * rk4 where rk4 = 58 (3 fields) / 62 (2 fields) per
-    point-field, +24 / +18 with the e^{i dk z} factor; per round trip and
+    point-field, +24 / +18 with the e^{i dk z} factor, +52 / +44 with the Kerr
+    terms; per round trip and
     point-field: cavity FFT pair 10 log2 N plus 6 (spectral factor) plus 6
     (mirror).
     """
@@ -75,6 +76,10 @@ def flops_per_roundtrip(cfg):
         rk4 = 58.0 + (24.0 if cfg.dk != 0 else 0.0)
     else:
         rk4 = 62.0 + (18.0 if cfg.dk != 0 else 0.0)
+    if getattr(cfg, "n2", 0.0) != 0.0:
+        # Kerr terms per stage and point-field: |A|^2 (3), sum_y G_xy |A_y|^2
+        # (2F), g A into the stage value (4)
+        rk4 += 4.0 * (3.0 + 2.0 * F + 4.0)
     per_step = 10.0 * lg + 6.0 + 2.0 * rk4
     per_rt = 10.0 * lg + 12.0
     return n * F * (nz * per_step + per_rt)
@@ -290,6 +295,7 @@ def main():
         extras = single_and_plain(args, opo, W, base, prec, local, torch)
         extras["e2e"] = e2e(args, opo, W, ctxs, batch, base, torch, np)
         extras["batched_sweep"] = sweep_leg(opo, W, prec, local, torch)
+        extras["variants_2e14"] = rows_leg(opo, W, prec, local, torch, base, cluster, th_req)
         extras["serving"] = serving_leg(prec, local, value, base)
     if rank == 0:
         line = {
@@ -392,6 +398,57 @@ def e2e(args, opo, W, ctxs, batch, base, torch, np):
             "h2d_bytes_per_step": B * F * n * 16,
             "d2h_bytes_per_step": B * (n * 16 + 32),
             "ms_per_step": dt * 1e3}
+
+
+def rows_leg(opo, W, prec, local, torch, base, cluster, threads, rounds=2):
+    """The widened entry and nonlinear-step variants on the 2^14 workload, in
+    the headline's launch shape: ns-pulsed pump (the Gaussian slice evaluated
+    at every entry), pump-resonant cavity (input added to the circulating
+    pump), Kerr terms with fourth-order dispersion, and the chi(2)-only
+    workload timed the same way for comparison.  Batch throughput (best of
+    three runs of ``rounds`` round trips, L2 not flushed) and the fraction of
+    the FP32 peak by each variant's own FLOP count."""
+    variants = {
+        "chi2_only_same_leg": base,
+        "ns_pulsed_pump": base.replace(pump_kind=W.PUMP_NS, pump_fwhm=10e-9,
+                                       pump_t0=30e-9),
+        "pump_resonant_tro": base.replace(resonant_mask=0b111, R=(0.9, 0.98, 0.98),
+                                          pump_power=0.05 * base.pump_power),
+        "kerr_beta4": base.replace(n2=2e-19, beta4=(4e-55, -3e-55, 2e-55)),
+    }
+    peak = SMS * FP32_LANES * 2 * PEAK_SM_MHZ * 1e6 / 1e12
+    out = {}
+    for name, cfg in variants.items():
+        s = torch.cuda.Stream()
+        probe = opo.Context(cfg, precision=prec, device=local, stream=s.cuda_stream)
+        ctxs = [probe]
+        try:
+            active, cl = opo.opo_fused_capacity(probe.h, cluster, threads)
+            ctxs += [opo.Context(cfg.replace(instance=i), precision=prec, device=local,
+                                 stream=s.cuda_stream) for i in range(1, active)]
+            b = opo.opo_batch_create([c.h for c in ctxs], cl, threads)
+            sec = 1e30
+            with torch.cuda.stream(s):
+                opo.opo_batch_run(b, 1)
+                for _ in range(3):  # best of three
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    opo.opo_batch_run(b, rounds)
+                    e1.record(s)
+                    e1.synchronize()
+                    sec = min(sec, e0.elapsed_time(e1) * 1e-3)
+            opo.opo_batch_destroy(b)
+            fs = active * cfg.nfields * cfg.nz * rounds / sec
+            tflops = flops_per_roundtrip(cfg) * active * rounds / sec / 1e12
+            out[name] = {"instances": active, "cluster": cl, "field_steps_per_s": fs,
+                         "tflops": tflops, "frac_fp32_peak": tflops / peak}
+        except opo.OPOError as e:
+            out[name] = {"error": str(e)}
+        finally:
+            for c in ctxs:
+                c.close()
+    return out
 
 
 def sweep_leg(opo, W, prec, local, torch, rounds=2):
