@@ -217,6 +217,28 @@ void orc_crystal_pass(const orc_params *p, double *fields)
     }
 }
 
+void orc_crystal_k(const orc_params *p, int32_t k, orc_params *q)
+{
+    *q = *p;
+    if (k < 1 || k > p->nextra)
+        return;
+    const orc_crystal *c = &p->extra[k - 1];
+    q->length = c->length;
+    q->nz = c->nz;
+    q->dk = c->dk;
+    q->deff = c->deff;
+    for (int x = 0; x < 3; x++) {
+        q->nidx[x] = c->nidx[x];
+        q->alpha[x] = c->alpha[x];
+        q->dbeta1[x] = c->dbeta1[x];
+        q->beta2[x] = c->beta2[x];
+        q->beta3[x] = c->beta3[x];
+        q->beta4[x] = c->beta4[x];
+    }
+    q->tod_div = c->tod_div;
+    q->n2 = c->n2;
+}
+
 /* ---------------------------------------------------------- pump / obs --- */
 
 void orc_pump_profile(const orc_params *p, int32_t kind, double power, double fwhm, double *out)
@@ -349,7 +371,11 @@ int orc_run(const orc_params *p, double *fields, const double *pump_in,
             else
                 memset(a, 0, sizeof(double) * fsz);
         }
-        orc_crystal_pass(p, fields);
+        for (int32_t k = 0; k <= p->nextra; k++) {
+            orc_params q;
+            orc_crystal_k(p, k, &q);
+            orc_crystal_pass(&q, fields);
+        }
         /* output-coupled fields and per-round-trip observables */
         double rec[4] = {0.0, 0.0, 0.0, 0.0};
         for (int x = 0; x < F; x++) {

@@ -30,6 +30,25 @@
 extern "C" {
 #endif
 
+/* Parameters of one nonlinear crystal of the round trip (the same meaning
+ * as the crystal fields of orc_params). */
+typedef struct {
+    double  length;
+    int32_t nz;
+    double  dk;
+    double  deff;
+    double  nidx[3];
+    double  alpha[3];
+    double  dbeta1[3];
+    double  beta2[3];
+    double  beta3[3];
+    double  beta4[3];
+    double  tod_div;
+    double  n2;
+} orc_crystal;
+
+#define ORC_MAX_EXTRA 7
+
 typedef struct {
     int32_t n;              /* grid points N (power of two)                       */
     int32_t nfields;        /* 2 (degenerate) or 3                                */
@@ -65,6 +84,11 @@ typedef struct {
      * Sec. 2.1): fourth-order dispersion and the Kerr index */
     double  beta4[3];       /* fourth derivative of k_x [s^4/m]                   */
     double  n2;             /* Kerr index [m^2/W]; 0: no chi(3) terms             */
+    /* further crystals passed after the first one in every round trip
+     * (Sec. 5: one or more nonlinear media in the cavity); the fields go on
+     * unchanged from one crystal to the next and z restarts at 0 in each */
+    int32_t nextra;
+    orc_crystal extra[ORC_MAX_EXTRA];
 } orc_params;
 
 /* In-place DFT of length n (power of two).  dir = -1: forward, unnormalized,
@@ -92,6 +116,10 @@ void orc_rk4_step(const orc_params *p, double *fields, double z0, double h);
 /* One crystal pass: nz symmetrized steps N/2 - L - N/2. */
 void orc_crystal_pass(const orc_params *p, double *fields);
 
+/* q <- p with the crystal fields replaced by those of crystal k (0: the
+ * first crystal, i.e. p itself; 1..nextra: extra[k-1]). */
+void orc_crystal_k(const orc_params *p, int32_t k, orc_params *q);
+
 /* Input pump profile.  kind 0: CW, 1: sech^2 (peak power), power [W],
  * fwhm [s] (intensity FWHM, sech^2 only).  out: n complex values. */
 void orc_pump_profile(const orc_params *p, int32_t kind, double power,
@@ -114,7 +142,8 @@ void orc_pump_slice(const orc_params *p, const double *pump_in, int64_t m, doubl
 /* Run round trips m0 .. m0+M-1.  fields: F*n complex, in/out (state at the
  * start of the next round trip).  pump_in: n complex (ignored for an
  * ns-pulsed pump).  Entry: a non-resonant pump is replaced by the input
- * pump, a resonant pump (pump-resonant cavity) gets it added.  trace (optional):
+ * pump, a resonant pump (pump-resonant cavity) gets it added.  The crystal
+ * pass goes through crystal 0, then the extra crystals in order.  trace (optional):
  * M rows of {P_p_out, P_s_out, P_i_out, nu_c}.  out_fields (optional): F*n
  * complex output-coupled fields of the last round trip.  Returns 0, or 1 if a
  * non-finite value appeared (the run stops at that round trip). */

@@ -18,6 +18,27 @@ from . import build as _build
 _lib = None
 
 
+class Crystal(ctypes.Structure):
+    """Mirror of ``orc_crystal`` in opo_oracle.h."""
+    _fields_ = [
+        ("length", ctypes.c_double),
+        ("nz", ctypes.c_int32),
+        ("dk", ctypes.c_double),
+        ("deff", ctypes.c_double),
+        ("nidx", ctypes.c_double * 3),
+        ("alpha", ctypes.c_double * 3),
+        ("dbeta1", ctypes.c_double * 3),
+        ("beta2", ctypes.c_double * 3),
+        ("beta3", ctypes.c_double * 3),
+        ("beta4", ctypes.c_double * 3),
+        ("tod_div", ctypes.c_double),
+        ("n2", ctypes.c_double),
+    ]
+
+
+MAX_EXTRA = 7
+
+
 class Params(ctypes.Structure):
     """Mirror of ``orc_params`` in opo_oracle.h."""
     _fields_ = [
@@ -49,6 +70,8 @@ class Params(ctypes.Structure):
         ("ns_t0", ctypes.c_double),
         ("beta4", ctypes.c_double * 3),
         ("n2", ctypes.c_double),
+        ("nextra", ctypes.c_int32),
+        ("extra", Crystal * MAX_EXTRA),
     ]
 
 
@@ -70,6 +93,7 @@ def lib():
         L.orc_linear_step.argtypes = [_P, _D, ctypes.c_double]
         L.orc_rk4_step.argtypes = [_P, _D, ctypes.c_double, ctypes.c_double]
         L.orc_crystal_pass.argtypes = [_P, _D]
+        L.orc_crystal_k.argtypes = [_P, ctypes.c_int32, _P]
         L.orc_pump_profile.argtypes = [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _D]
         L.orc_power.argtypes = [_P, ctypes.c_int32, _D]
         L.orc_power.restype = ctypes.c_double
@@ -122,6 +146,25 @@ def params(cfg, tod_div=6.0):
         p.ns_a0 = (2.0 * inten / (p.nidx[0] * 8.8541878128e-12 * 299792458.0)) ** 0.5
         p.ns_fwhm = float(cfg.pump_fwhm)
         p.ns_t0 = float(g("pump_t0"))
+    # further crystals: objects with the crystal attribute names above
+    extra = list(g("extra_crystals", ()))
+    if len(extra) > MAX_EXTRA:
+        raise ValueError("at most %d extra crystals" % MAX_EXTRA)
+    p.nextra = len(extra)
+    for i, c in enumerate(extra):
+        e = p.extra[i]
+        e.length = float(c.length)
+        e.nz = int(c.nz)
+        e.dk = float(getattr(c, "dk", 0.0))
+        e.deff = float(c.deff)
+        e.nidx = _trip(c.nidx)
+        e.alpha = _trip(getattr(c, "alpha", (0, 0, 0)))
+        e.dbeta1 = _trip(getattr(c, "dbeta1", (0, 0, 0)))
+        e.beta2 = _trip(getattr(c, "beta2", (0, 0, 0)))
+        e.beta3 = _trip(getattr(c, "beta3", (0, 0, 0)))
+        e.beta4 = _trip(getattr(c, "beta4", (0, 0, 0)))
+        e.tod_div = float(tod_div)
+        e.n2 = float(getattr(c, "n2", 0.0))
     return p
 
 
@@ -171,6 +214,13 @@ def crystal_pass(p, fields):
     return a
 
 
+def crystal_k(p, k):
+    """Params with the crystal fields of crystal k (0: the first)."""
+    q = Params()
+    lib().orc_crystal_k(ctypes.byref(p), int(k), ctypes.byref(q))
+    return q
+
+
 def pump_profile(p, kind, power, fwhm=0.0):
     out = np.zeros(p.n, dtype=np.complex128)
     lib().orc_pump_profile(ctypes.byref(p), int(kind), float(power), float(fwhm), _ptr(out))
@@ -213,7 +263,7 @@ def run(p, fields, pump_in, m0=0, M=1):
     return a, trace[: int(M)], out, int(st)
 
 
-__all__ = ["Params", "params", "fft", "kappa", "omega", "linear_step", "rk4_step",
-           "crystal_pass", "pump_profile", "pump_slice", "power", "centroid", "cavity", "run",
-           "lib"]
+__all__ = ["Params", "Crystal", "params", "fft", "kappa", "omega", "linear_step", "rk4_step",
+           "crystal_pass", "crystal_k", "pump_profile", "pump_slice", "power", "centroid",
+           "cavity", "run", "lib"]
 

@@ -58,6 +58,24 @@ def noise(n: int, amp: float, seed: int, instance: int = 0, fld: int = 1) -> np.
     return (amp / math.sqrt(2.0)) * g
 
 
+@dataclass(frozen=True)
+class Crystal:
+    """A further nonlinear crystal of the round trip (after the configuration's
+    own): its length, step count, phase mismatch, d_eff, indices, loss,
+    dispersion and Kerr index.  Wavelengths are the configuration's."""
+    length: float = 5e-3
+    nz: int = 50
+    dk: float = 0.0
+    deff: float = 14e-12
+    nidx: tuple = (2.15, 2.14, 2.08)
+    alpha: tuple = (0.0, 0.0, 0.0)
+    dbeta1: tuple = (0.0, 0.0, 0.0)
+    beta2: tuple = (0.0, 0.0, 0.0)
+    beta3: tuple = (0.0, 0.0, 0.0)
+    beta4: tuple = (0.0, 0.0, 0.0)
+    n2: float = 0.0
+
+
 @dataclass
 class OPOConfig:
     """One OPO instance: grid, crystal and cavity, SI units.
@@ -81,6 +99,7 @@ class OPOConfig:
     beta3: tuple = (0.0, 0.0, 0.0)
     beta4: tuple = (0.0, 0.0, 0.0)
     n2: float = 0.0
+    extra_crystals: tuple = ()   # Crystal objects passed after this one
     w0: float = 55e-6
     resonant_mask: int = 0b010
     R: tuple = (0.0, 0.98, 0.0)
@@ -242,6 +261,6 @@ PRESETS = {
     "tro_cw": tro_cw,
 }
 
-__all__ = ["OPOConfig", "noise", "sro_threshold_power", "PRESETS", "cw_sro_1024", "cw_sro_16k",
+__all__ = ["OPOConfig", "Crystal", "noise", "sro_threshold_power", "PRESETS", "cw_sro_1024", "cw_sro_16k",
            "sync_pumped_64k", "degenerate_2field", "ns_pulsed_degenerate", "tro_cw",
            "sweep_instances", "EPS0", "C0", "PUMP_CW", "PUMP_SECH2", "PUMP_USER", "PUMP_NS"]

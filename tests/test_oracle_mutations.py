@@ -44,6 +44,12 @@ MUTANTS = [
     ("XPM counted once", "itot += 2.0 * inten[y];", "itot += 1.0 * inten[y];"),
     ("Kerr k0 of the signal", "double k0 = 2.0 * ORC_PI / p->lambda[x];",
      "double k0 = 2.0 * ORC_PI / p->lambda[1];"),
+    ("extra crystals skipped", "for (int32_t k = 0; k <= p->nextra; k++) {",
+     "for (int32_t k = 0; k <= 0 * p->nextra; k++) {"),
+    ("extra crystal keeps the first one's dispersion", "q->beta2[x] = c->beta2[x];",
+     "q->beta2[x] = p->beta2[x];"),
+    ("extra crystal keeps the first one's indices", "q->nidx[x] = c->nidx[x];",
+     "q->nidx[x] = p->nidx[x];"),
 ]
 
 

@@ -499,6 +499,85 @@ def test_kerr_keeps_chi2_exchange_and_total_power(orc):
     assert rel_l2(orc.crystal_pass(q, A), out) > 1e-3
 
 
+# ------------------------------------------- several crystals per round trip
+
+def _as_crystal(cfg, **kw):
+    d = dict(length=cfg.length, nz=cfg.nz, dk=cfg.dk, deff=cfg.deff, nidx=cfg.nidx,
+             alpha=cfg.alpha, dbeta1=cfg.dbeta1, beta2=cfg.beta2, beta3=cfg.beta3,
+             beta4=cfg.beta4, n2=cfg.n2)
+    d.update(kw)
+    return W.Crystal(**d)
+
+
+def test_crystal_split_in_two_equals_the_whole(orc):
+    """With dk = 0 the step sequence of a crystal cut into two equal halves
+    (z restarting in the second) is the same as the whole crystal's: the
+    round trip must agree bit for bit."""
+    whole = W.cw_sro_16k().replace(n=256, nz=20, n2=1e-19, beta4=(1e-55, 0, 0),
+                                   alpha=(0.5, 0.2, 0.1))
+    half = whole.replace(length=whole.length / 2, nz=10)
+    split = half.replace(extra_crystals=(_as_crystal(half),))
+    rng = np.random.default_rng(3)
+    A = 1e6 * (rng.standard_normal((3, 256)) + 1j * rng.standard_normal((3, 256)))
+    pa, pb = orc.params(whole), orc.params(split)
+    pump = orc.pump_profile(pa, 0, whole.pump_power)
+    a, ta, oa, _ = orc.run(pa, A, pump, 0, 2)
+    b, tb, ob, _ = orc.run(pb, A, pump, 0, 2)
+    assert np.array_equal(a, b) and np.array_equal(ta, tb) and np.array_equal(oa, ob)
+
+
+def test_two_crystals_undepleted_gain_closed_form(orc):
+    """Undepleted pump, two crystals with different dk, d_eff and indices, z
+    restarting in each: per crystal (u, w) = (A_s e^{-i dk z/2},
+    A_i* e^{+i dk z/2}) obey d/dz (u, w) = M (u, w) with
+    M = [[-i dk/2, i k_s A_p], [-i k_i A_p*, i dk/2]], so each crystal maps
+    (A_s, A_i*) by a 2x2 matrix exponential; the pass is their product."""
+    from scipy.linalg import expm
+    c1 = W.OPOConfig(n=4, nz=400, length=8e-3, dk=300.0, deff=14e-12)
+    c2 = _as_crystal(c1, length=5e-3, nz=300, dk=-150.0, deff=-20e-12,
+                     nidx=(2.2, 2.18, 2.1))
+    cfg = c1.replace(extra_crystals=(c2,))
+    p = orc.params(cfg)
+    ap = 3e6 * np.exp(0.4j)
+    as0, ai0 = 1.0 + 0.5j, -0.3 + 0.2j
+    A = np.stack([np.full(4, ap), np.full(4, as0), np.full(4, ai0)])
+    out = orc.crystal_pass(p, A)
+    out = orc.crystal_pass(orc.crystal_k(p, 1), out)
+    v = np.array([as0, np.conj(ai0)])
+    for (L, dk, deff, nidx) in ((c1.length, c1.dk, c1.deff, c1.nidx),
+                                (c2.length, c2.dk, c2.deff, c2.nidx)):
+        ks = 2 * math.pi * deff / (nidx[1] * c1.lam[1])
+        ki = 2 * math.pi * deff / (nidx[2] * c1.lam[2])
+        M = np.array([[-0.5j * dk, 1j * ks * ap], [-1j * ki * np.conj(ap), 0.5j * dk]])
+        uw = expm(M * L) @ v
+        v = np.array([uw[0] * np.exp(0.5j * dk * L), uw[1] * np.exp(-0.5j * dk * L)])
+    assert abs(out[1][0] - v[0]) <= 1e-9 * abs(v[0])
+    assert abs(np.conj(out[2][0]) - v[1]) <= 1e-9 * abs(v[1])
+    # and the run loop passes through both crystals
+    pump = np.full(4, ap)
+    A2 = A.copy()
+    A2[0] = ap
+    r, _, _, _ = orc.run(orc.params(cfg.replace(resonant_mask=0b111, R=(1.0, 1.0, 1.0))), A2,
+                         0 * pump, 0, 1)
+    assert abs(r[1][0] - v[0]) <= 1e-9 * abs(v[0])
+
+
+def test_dispersion_of_two_crystals_adds(orc):
+    """deff = 0: a single Fourier mode turns by sum_k L_k phi_k(Omega)."""
+    n, T = 64, 100e-12
+    c1 = W.OPOConfig(n=n, nz=7, length=3e-3, deff=0.0, beta2=(0, 2e-25, 0))
+    c2 = _as_crystal(c1, length=4e-3, nz=9, beta2=(0, 0, 0), beta3=(0, 5e-39, 0),
+                     dbeta1=(0, 1e-12, 0))
+    cfg = c1.replace(extra_crystals=(c2,), resonant_mask=0b111, R=(1.0, 1.0, 1.0))
+    p = orc.params(cfg)
+    k = 5
+    om = 2 * math.pi * k / T
+    a = np.stack([np.zeros(n), np.exp(2j * np.pi * k * np.arange(n) / n), np.zeros(n)])
+    r, _, _, _ = orc.run(p, a, np.zeros(n), 0, 1)
+    phi = c1.length * 2e-25 * om ** 2 / 2 + c2.length * (-1e-12 * om - 5e-39 * om ** 3 / 6)
+    assert np.max(np.abs(r[1] - a[1] * np.exp(1j * phi))) <= 1e-11
+
+
 # ------------------------- ns-pulsed pump and pump-resonant (TRO) entry
 
 def _ns_cfg(n=64, **kw):
