@@ -10,7 +10,8 @@
  *                  circulating one; a non-resonant signal/idler restarts from
  *                  zero (Sec. 2.1, boundary conditions apply to resonant
  *                  fields only)
- *   crystal pass . nz fixed steps of the symmetrized split-step Fourier
+ *   crystal pass . (per crystal, in order, when several are set) nz fixed
+ *                  steps of the symmetrized split-step Fourier
  *                  method N/2 - L - N/2 (Sec. 2.2, Eq. (expon)) on the
  *                  coupled-wave equations (Sec. 2.1, Eqs. (CEp)-(CEi));
  *                  linear operator of Eq. (linearop) in the frequency domain,
@@ -93,6 +94,7 @@ enum { OPO_FP64 = 0, OPO_FP32_PH64 = 1 };               /* opo_grid.precision */
  * at t = m t_rt + tau_n in round trip m. */
 enum { OPO_PUMP_CW = 0, OPO_PUMP_SECH2 = 1, OPO_PUMP_USER = 2, OPO_PUMP_NS = 3 };
 enum { OPO_INTRACAVITY = 0, OPO_OUTPUT = 1 };           /* opo_get_fields which */
+#define OPO_MAX_CRYSTALS 8  /* crystals per round trip (opo_set_crystals) */
 enum { OPO_PATH_AUTO = 0, OPO_PATH_PLAIN = 1, OPO_PATH_FUSED = 2 };
 
 /* Grid and numerics of one OPO instance (Sec. 2.4). */
@@ -169,6 +171,19 @@ OPO_API int opo_create(opo_ctx **out, const opo_grid *grid);
 /* Set the crystal (Sec. 2.1); rebuilds the per-step dispersion factors D_x
  * (FP64 arguments, one rounding) on the device.  Copies *crystal. */
 OPO_API int opo_set_crystal(opo_ctx *ctx, const opo_crystal *crystal);
+
+/* Several nonlinear crystals per round trip (the paper notes that one or
+ * more nonlinear media can be placed in the cavity): count in
+ * [1, OPO_MAX_CRYSTALS] crystals, passed in array order every round trip.
+ * The fields go on unchanged from one crystal to the next (no interface or
+ * free-space step between them) and z of the e^{i dk z} factor restarts at 0
+ * in each.  Every crystal keeps its own length, steps, dk, d_eff, indices,
+ * loss, dispersion and Kerr index; lambda_m must be the same in all of them
+ * (the same fields), and the input pump amplitude and the output powers use
+ * crystals[0]'s indices and waist.  opo_set_crystal(ctx, k) is
+ * opo_set_crystals(ctx, k, 1).  OPO_E_INVALID for a bad count, a bad crystal
+ * or differing wavelengths.  Copies the array. */
+OPO_API int opo_set_crystals(opo_ctx *ctx, const opo_crystal *crystals, int32_t count);
 
 /* Set the cavity and pump (Eq. (BC), Sec. 2.3); rebuilds the input pump, GDD
  * and delay factors on the device.  Copies *cavity and pump_user. */

@@ -93,6 +93,14 @@ void free_all(opo_ctx *c)
     for (void *b : bufs)
         if (b)
             cudaFree(b);
+    for (int k = 1; k < opo::kMaxCry; k++) {
+        opo::CrystalState &x = c->xs[k];
+        for (void *b : {x.disp, x.disp_t, x.ekz})
+            if (b)
+                cudaFree(b);
+    }
+    if (c->d_cry)
+        cudaFree(c->d_cry);
     if (c->h_pinned)
         cudaFreeHost(c->h_pinned);
     if (c->graph)
@@ -122,6 +130,21 @@ int derive(opo_ctx *c)
     d.use_dk = k.dk_per_m != 0.0;
     d.eom = v.eom_beta_rad != 0.0;
     d.kerr = kerr_coefficients(k, c->F, d.kerr_g);
+    // every crystal's descriptor (device pointers are filled in by the table
+    // setup); the specialised kernels take the Kerr instantiation when any
+    // crystal has the terms
+    c->kerr_any = false;
+    for (int i = 0; i < c->ncry; i++) {
+        const opo_crystal &ki = c->cry[i];
+        CryDesc &cd = c->h_cry[i];
+        for (int x = 0; x < 3; x++)
+            cd.kappa[x] = (x < c->F) ? 2.0 * kPi * ki.deff_mpv / (ki.n[x] * ki.lambda_m[x]) : 0.0;
+        cd.h = 0.5 * ki.length_m / (double)ki.nz;
+        cd.nz = ki.nz;
+        cd.use_dk = ki.dk_per_m != 0.0;
+        cd.kerr = kerr_coefficients(ki, c->F, cd.kerr_g);
+        c->kerr_any = c->kerr_any || cd.kerr;
+    }
     d.ns = NsPump{};
     d.ns.n = c->n;
     d.ns.dt = c->grid.t_window_s / (double)c->n;
@@ -258,7 +281,7 @@ int choose_path(opo_ctx *c, FusedCfg *cfg)
     if (c->path_req == OPO_PATH_PLAIN)
         return OPO_PATH_PLAIN;
     bool ok = fused_config(c->csz, c->F, c->F, c->n, c->n, c->cluster_req, c->rtpl_req,
-                           c->threads_req, c->dv.kerr, cfg);
+                           c->threads_req, c->kerr_any, cfg);
     if (c->path_req == OPO_PATH_FUSED)
         return ok ? OPO_PATH_FUSED : -1;
     return ok ? OPO_PATH_FUSED : OPO_PATH_PLAIN;
@@ -389,34 +412,73 @@ int opo_destroy(opo_ctx *c)
     return OPO_OK;
 }
 
+// Make *p hold at least bytes (re-allocating after the stream drained).
+static int ensure_buf(opo_ctx *c, void **p, int *cap, int want, size_t elem)
+{
+    if (*p && (!cap || want <= *cap))
+        return OPO_OK;
+    cudaStreamSynchronize(c->stream);
+    if (*p)
+        cudaFree(*p);
+    *p = nullptr;
+    if (cap)
+        *cap = 0;
+    if (cudaMalloc(p, elem * (size_t)want) != cudaSuccess) {
+        *p = nullptr;
+        return OPO_E_NOMEM;
+    }
+    if (cap)
+        *cap = want;
+    return OPO_OK;
+}
+
+int opo_set_crystals(opo_ctx *c, const opo_crystal *list, int32_t count)
+{
+    if (!c || !list || count < 1 || count > OPO_MAX_CRYSTALS)
+        return OPO_E_INVALID;
+    for (int i = 0; i < count; i++) {
+        if (!valid_crystal(c, &list[i]))
+            return OPO_E_INVALID;
+        for (int x = 0; x < c->F; x++)
+            if (list[i].lambda_m[x] != list[0].lambda_m[x])
+                return OPO_E_INVALID; // the same fields in every crystal
+    }
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    // device buffers first, so that a failure leaves the old crystals intact
+    int rc = ensure_buf(c, &c->d_ekz, &c->ekz_cap, 4 * list[0].nz + 1, c->csz);
+    const size_t fb = c->csz * (size_t)c->F * c->n;
+    for (int i = 1; i < count && rc == OPO_OK; i++) {
+        opo::CrystalState &x = c->xs[i];
+        rc = ensure_buf(c, &x.disp, nullptr, 1, fb);
+        if (rc == OPO_OK)
+            rc = ensure_buf(c, &x.disp_t, nullptr, 1, fb);
+        if (rc == OPO_OK)
+            rc = ensure_buf(c, &x.ekz, &x.ekz_cap, 4 * list[i].nz + 1, c->csz);
+    }
+    if (rc == OPO_OK && !c->d_cry)
+        rc = ensure_buf(c, (void **)&c->d_cry, nullptr, 1, sizeof(opo::CryDesc) * opo::kMaxCry);
+    if (rc != OPO_OK)
+        return rc;
+    for (int i = 0; i < count; i++)
+        c->cry[i] = list[i];
+    c->crystal = list[0];
+    c->ncry = count;
+    c->have_crystal = true;
+    c->graph_valid = false;
+    derive(c);
+    rc = setup_crystal_tables(c);
+    if (rc == OPO_OK && c->have_cavity)
+        rc = setup_cavity_tables(c); // pump amplitude depends on n_p and w0
+    return rc;
+}
+
 int opo_set_crystal(opo_ctx *c, const opo_crystal *k)
 {
     if (!c || !k)
         return OPO_E_INVALID;
-    if (!valid_crystal(c, k))
-        return OPO_E_INVALID;
-    DeviceGuard g(c->device);
-    if (!g.ok)
-        return OPO_E_CUDA;
-    c->crystal = *k;
-    int cnt = 4 * k->nz + 1;
-    if (cnt > c->ekz_cap) {
-        cudaStreamSynchronize(c->stream);
-        if (c->d_ekz)
-            cudaFree(c->d_ekz);
-        c->d_ekz = nullptr;
-        c->ekz_cap = 0;
-        if (cudaMalloc(&c->d_ekz, c->csz * cnt) != cudaSuccess)
-            return OPO_E_NOMEM;
-        c->ekz_cap = cnt;
-    }
-    c->have_crystal = true;
-    c->graph_valid = false;
-    derive(c);
-    int rc = setup_crystal_tables(c);
-    if (rc == OPO_OK && c->have_cavity)
-        rc = setup_cavity_tables(c); // pump amplitude depends on n_p and w0
-    return rc;
+    return opo_set_crystals(c, k, 1);
 }
 
 int opo_set_cavity(opo_ctx *c, const opo_cavity *v)
@@ -543,7 +605,7 @@ int opo_set_path(opo_ctx *c, int32_t path, int32_t cluster, int32_t rt_per_launc
         FusedCfg cfg;
         DeviceGuard g(c->device);
         if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, rt_per_launch, threads,
-                          c->dv.kerr, &cfg))
+                          c->kerr_any, &cfg))
             return OPO_E_UNSUPPORTED;
     }
     c->path_req = path;
@@ -639,7 +701,7 @@ int opo_fused_capacity(const opo_ctx *c, int32_t cluster, int32_t threads, int32
     if (!g.ok)
         return OPO_E_CUDA;
     FusedCfg cfg;
-    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, threads, c->dv.kerr, &cfg))
+    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, threads, c->kerr_any, &cfg))
         return OPO_E_UNSUPPORTED;
     *max_active = fused_max_active(c->prec == OPO_FP64, c->F, c->n, cfg);
     if (cluster_out)
@@ -743,14 +805,14 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
             const opo_ctx *g0 = b->groups[k].ctxs[0];
             int cl0, th0, rt0;
             want(g0, &cl0, &th0, &rt0);
-            if (g0->n == c->n && g0->F == c->F && g0->dv.kerr == c->dv.kerr && cl0 == cl &&
+            if (g0->n == c->n && g0->F == c->F && g0->kerr_any == c->kerr_any && cl0 == cl &&
                 th0 == th && rt0 == rt)
                 gi = (int)k;
         }
         if (gi < 0) {
             b->groups.emplace_back();
             gi = (int)b->groups.size() - 1;
-            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, c->dv.kerr,
+            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, c->kerr_any,
                               &b->groups[gi].cfg)) {
                 batch_free(b);
                 return OPO_E_UNSUPPORTED;

@@ -29,14 +29,21 @@ __host__ __device__ __forceinline__ V cmk(typename cscal<V>::type re, typename c
 }
 template <class V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
 template <class V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+// Fused multiply-add with the rounding fixed in the source: a sum of two
+// products a b + c d can be contracted two ways, and the compiler may choose
+// differently in two inlined copies of the same arithmetic; spelling the
+// fma out makes every copy (first or later round trip of a launch, last step
+// of a crystal, one or many instances) round the same.
+__device__ __forceinline__ float fmad_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmad_(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <class V> __device__ __forceinline__ V cmul(V a, V b)
 {
-    return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return cmk<V>(fmad_(a.x, b.x, -(a.y * b.y)), fmad_(a.x, b.y, a.y * b.x));
 }
 // a * conj(b)
 template <class V> __device__ __forceinline__ V cmulc(V a, V b)
 {
-    return cmk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    return cmk<V>(fmad_(a.x, b.x, a.y * b.y), fmad_(a.y, b.x, -(a.x * b.y)));
 }
 template <class V> __device__ __forceinline__ V cconj(V a) { return cmk<V>(a.x, -a.y); }
 template <class V> __device__ __forceinline__ V cscale(V a, typename cscal<V>::type s)
@@ -47,7 +54,7 @@ template <class V> __device__ __forceinline__ V cscale(V a, typename cscal<V>::t
 template <class V> __device__ __forceinline__ V cmuli(V a) { return cmk<V>(-a.y, a.x); }
 template <class V> __device__ __forceinline__ typename cscal<V>::type cabs2(V a)
 {
-    return a.x * a.x + a.y * a.y;
+    return fmad_(a.x, a.x, a.y * a.y);
 }
 
 // ------------------------------------------------- in-register DFTs ----
@@ -73,7 +80,7 @@ __device__ __forceinline__ V rot16(V x)
     } else {
         const S c = (S)c16[A];
         const S s = (S)(DIR * s16[A]);
-        return cmk<V>(x.x * c - x.y * s, x.x * s + x.y * c);
+        return cmk<V>(fmad_(x.x, c, -(x.y * s)), fmad_(x.x, s, x.y * c));
     }
 }
 
@@ -235,7 +242,7 @@ __device__ __forceinline__ void rk4_point_kerr(V *y, V e0, V e1, V e2,
 #pragma unroll
             for (int z = 0; z < F; z++)
                 g += G[3 * x + z] * i2[z];
-            q[x] = cmk<V>(c[x] * p[x].x + g * a[x].x, c[x] * p[x].y + g * a[x].y);
+            q[x] = cmk<V>(fmad_(c[x], p[x].x, g * a[x].x), fmad_(c[x], p[x].y, g * a[x].y));
         }
     };
     const S hh = h * (S)0.5, h6 = h / (S)6;
@@ -350,7 +357,7 @@ struct NsPump {
 template <class T>
 __device__ __forceinline__ cv<T> ns_pump_at(const NsPump &q, int g, int64_t m)
 {
-    const double t = (double)m * q.t_rt + (double)(g - q.n / 2) * q.dt - q.t0;
+    const double t = __fma_rn((double)m, q.t_rt, (double)(g - q.n / 2) * q.dt - q.t0);
     const double x = q.c * t * t;
     T a;
     if constexpr (sizeof(T) == 8)

@@ -103,14 +103,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             Dsm[i] = gD[(size_t)f * n + (c << logPc) + k1l + ((size_t)k2 << logP)];
         }
     }
-    const T kap[3] = {(T)d.kappa[0], (T)d.kappa[1], (T)d.kappa[2]};
-    const T h = (T)d.h;
-    const bool use_e = d.use_dk != 0;
-    const bool kerr = d.kerr != 0;
-    T kg[9];
-    for (int i = 0; i < 9; i++)
-        kg[i] = (T)d.kerr_g[i];
-    const V *ekz = (const V *)d.ekz;
+    // constants of the crystal being passed (several per round trip)
+    T kap[3], h, kg[9];
+    bool use_e = false, kerr = false;
+    const V *ekz = nullptr;
+    const V *gDk = gD;
+    int nzk = 0;
+    auto load_crystal = [&](int k) {
+        const CryDesc &cd = d.cry[k];
+        for (int x = 0; x < 3; x++)
+            kap[x] = (T)cd.kappa[x];
+        h = (T)cd.h;
+        use_e = cd.use_dk != 0;
+        kerr = cd.kerr != 0;
+        for (int i = 0; i < 9; i++)
+            kg[i] = (T)cd.kerr_g[i];
+        ekz = (const V *)cd.ekz;
+        gDk = (const V *)cd.disp;
+        nzk = cd.nz;
+    };
     const V *gG = (const V *)d.gdd;
     const V *gPump = (const V *)d.pump;
     const RadixPlan planP = make_plan(logP), planQ = make_plan(logQ);
@@ -176,7 +187,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     // transforms, push back into remote X, inverse column transforms.
     // Returns the buffer holding the time-domain result.  `spec` accumulates
     // the signal spectrum sums (cavity visit).
-    auto freq_visit_and_back = [&](bool use_gdd, double *acc) -> V * {
+    auto freq_visit_and_back = [&](bool use_gdd, double *acc, bool dsm) -> V * {
         // forward rows
         int Ns = 1;
         V *src = stages_but_last(FWD{}, false, Y, planQ, Q, F * Pc, Ns);
@@ -196,7 +207,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     acc[4] += (double)kk * p2;
                 }
             } else {
-                fac = disp_smem ? Dsm[(seq << logQ) + k2] : gD[(size_t)f * n + k];
+                fac = dsm ? Dsm[(seq << logQ) + k2] : gDk[(size_t)f * n + k];
             }
             dstb[addrC(seq, k2)] = cmul(v, fac);
         };
@@ -289,14 +300,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             }
         }
         __syncthreads();
-        // ---- crystal pass: nz symmetrized steps
-        for (int j = 0; j < d.nz; j++) {
-            rk4_half(X, 4 * j);
-            __syncthreads();
-            forward_to_Y();
-            V *res = freq_visit_and_back(false, nullptr);
-            rk4_half(res, 4 * j + 2);
-            __syncthreads();
+        // ---- crystal passes: nz symmetrized steps of every crystal in order
+        for (int kc = 0; kc < d.ncry; kc++) {
+            load_crystal(kc);
+            for (int j = 0; j < nzk; j++) {
+                rk4_half(X, 4 * j);
+                __syncthreads();
+                forward_to_Y();
+                V *res = freq_visit_and_back(false, nullptr, disp_smem && kc == 0);
+                rk4_half(res, 4 * j + 2);
+                __syncthreads();
+            }
         }
         // ---- observables: output power sums, non-finite check
         double acc[kNslot] = {0, 0, 0, 0, 0};
@@ -314,7 +328,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         __syncthreads();
         // ---- cavity: spectral visit (GDD, delay, signal spectrum sums)
         forward_to_Y();
-        V *res = freq_visit_and_back(true, acc);
+        V *res = freq_visit_and_back(true, acc, false);
         block_reduce5(acc, red);
         if (threadIdx.x == 0) {
             double *o = d.obs + (slot * C + c) * kNslot;
@@ -513,6 +527,8 @@ void fill_desc(InstDesc &d, const opo_ctx *c)
     d.kerr = c->dv.kerr;
     for (int i = 0; i < 9; i++)
         d.kerr_g[i] = c->dv.kerr_g[i];
+    d.cry = c->d_cry;
+    d.ncry = c->ncry;
 }
 
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s)

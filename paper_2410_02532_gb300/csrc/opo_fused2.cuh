@@ -111,15 +111,32 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     // ---- descriptor scalars into registers
     const InstDesc &dg = descs[inst];
     const unsigned resmask = dg.resmask;
-    const int nz = dg.nz;
-    const bool use_e = dg.use_dk != 0;
+    const int ncry = dg.ncry;
     const bool eom = dg.eom != 0;
     constexpr bool kerr = KR;
-    __shared__ T sG[KR ? 9 : 1]; // Kerr coefficients G_xy
-    if (KR && threadIdx.x < 9)
-        sG[threadIdx.x] = (T)dg.kerr_g[threadIdx.x];
-    const T kap[3] = {(T)dg.kappa[0], (T)dg.kappa[1], (T)dg.kappa[2]};
-    const T h = (T)dg.h;
+    // constants of every crystal of the round trip, in the field precision
+    struct CrySm {
+        T kap[3], h;
+        T G[KR ? 9 : 1]; // Kerr coefficients G_xy
+        const V *ekz;    // e^{i dk q dz/4}
+        const V *D;      // dispersion factors: row-major (IP) or natural order
+        int nz, use_e;
+    };
+    __shared__ CrySm sCry[kMaxCry];
+    if (threadIdx.x < ncry) {
+        const CryDesc &cd = dg.cry[threadIdx.x];
+        CrySm &s = sCry[threadIdx.x];
+        for (int x = 0; x < 3; x++)
+            s.kap[x] = (T)cd.kappa[x];
+        s.h = (T)cd.h;
+        if constexpr (KR)
+            for (int i = 0; i < 9; i++)
+                s.G[i] = (T)cd.kerr_g[i];
+        s.ekz = (const V *)cd.ekz;
+        s.D = (const V *)(IP ? cd.disp_t : cd.disp);
+        s.nz = cd.nz;
+        s.use_e = cd.use_dk;
+    }
     V bc[3], osc[3];
     for (int x = 0; x < 3; x++) {
         bc[x] = cmk<V>((T)dg.bc_re[x], (T)dg.bc_im[x]);
@@ -132,9 +149,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     const V *gPump = (const V *)dg.pump;
     const V *gD = (const V *)dg.disp;
     const V *gG = (const V *)dg.gdd;
-    const V *gDt = (const V *)dg.disp_t;
     const V *gGt = (const V *)dg.gdd_t;
-    const V *ekz = (const V *)dg.ekz;
     const V *gtw = (const V *)dg.tw;
     double *obs = dg.obs;
     int *err = dg.err;
@@ -187,12 +202,33 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
         return cmul(twHi[a >> LS], twLo[a & ((1u << LS) - 1)]);
     };
 
+    // ---- constants of the crystal being passed (registers, as for one
+    // crystal); set_crystal switches them where the next crystal begins
+    T kap[3], h;
+    bool use_e;
+    const V *ekz;
+    int kcur;
+    auto set_crystal = [&](int k) {
+        kcur = k;
+        for (int x = 0; x < 3; x++)
+            kap[x] = sCry[k].kap[x];
+        h = sCry[k].h;
+        use_e = sCry[k].use_e != 0;
+        ekz = sCry[k].ekz;
+    };
+
     // ---- block A: shared by every z-step boundary
     // mode 0: first round trip of the launch, input from global memory
     // mode 1: interior z-step boundary
     // mode 2: end of the crystal pass (observables, then cavity forward)
     // mode 3: end of the cavity visit of round trip m_cav (mirror, EOM, then
     //         entry of round trip m_cav + 1, or the final store)
+    // modes 5 and 6: a z-step boundary where one crystal ends and the next
+    //         begins, in two passes with the current crystal's constants
+    //         each: 5 ends the step (inverse column stage 2, RK4 half step)
+    //         and stores the time-domain values where it read them, 6 takes
+    //         them up again (RK4 half step of the next crystal, forward
+    //         column stage 1); each item stays with the same thread
     auto block_a = [&](auto mode_tag, int qa, int qb, int64_t m_cav, bool next_rt, bool save_out,
                        double *acc) {
         constexpr int mode = decltype(mode_tag)::value;
@@ -239,7 +275,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
         auto process = [&](int u, V (&v)[F][Ra1], bool own) -> bool {
             int b, j;
             dec(u, b, j);
-            if constexpr (mode != 0) {
+            if constexpr (mode != 0 && mode != 6) {
                 // inverse column stage 2: radix Ra1, Ns = Ra2, k = j
 #pragma unroll
                 for (int f = 0; f < F; f++) {
@@ -253,7 +289,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                 }
             }
             // time domain: v[f][r] at n1 = j + r Ra2
-            if constexpr (mode == 1 || mode == 2) {
+            if constexpr (mode == 1 || mode == 2 || mode == 5) {
 #pragma unroll
                 for (int r = 0; r < Ra1; r++) {
                     V y[F];
@@ -261,7 +297,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                     for (int f = 0; f < F; f++)
                         y[f] = v[f][r];
                     if constexpr (kerr)
-                        rk4_point_kerr<F>(y, e0a, e1a, e2a, kap, h, use_e, sG);
+                        rk4_point_kerr<F>(y, e0a, e1a, e2a, kap, h, use_e, sCry[kcur].G);
                     else
                         rk4_point<F>(y, e0a, e1a, e2a, kap, h, use_e);
 #pragma unroll
@@ -287,7 +323,8 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                     V mod = cmk<V>((T)1, (T)0);
                     if (eom) {
                         const int gi = gtime(j + r * Ra2, b);
-                        double uu = eom_f * ((double)(gi - N / 2) * dt) + eom_f * ((double)m_cav * t_rt);
+                        double uu = __fma_rn(eom_f, (double)(gi - N / 2) * dt,
+                                             eom_f * ((double)m_cav * t_rt));
                         double fr = uu - floor(uu);
                         T ph;
                         if constexpr (sizeof(T) == 8)
@@ -335,14 +372,14 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                         if (!(resmask & (1u << f)))
                             y[f] = cmk<V>((T)0, (T)0);
                     if constexpr (kerr)
-                        rk4_point_kerr<F>(y, e0b, e1b, e2b, kap, h, use_e, sG);
+                        rk4_point_kerr<F>(y, e0b, e1b, e2b, kap, h, use_e, sCry[kcur].G);
                     else
                         rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
 #pragma unroll
                     for (int f = 0; f < F; f++)
                         v[f][r] = y[f];
                 }
-            } else if constexpr (mode == 1) {
+            } else if constexpr (mode == 1 || mode == 6) {
 #pragma unroll
                 for (int r = 0; r < Ra1; r++) {
                     V y[F];
@@ -350,7 +387,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                     for (int f = 0; f < F; f++)
                         y[f] = v[f][r];
                     if constexpr (kerr)
-                        rk4_point_kerr<F>(y, e0b, e1b, e2b, kap, h, use_e, sG);
+                        rk4_point_kerr<F>(y, e0b, e1b, e2b, kap, h, use_e, sCry[kcur].G);
                     else
                         rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
 #pragma unroll
@@ -359,19 +396,31 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                 }
             }
             // forward column stage 1: radix Ra1, Ns = 1, outputs at j Ra1 + r
+            if constexpr (mode != 5) {
 #pragma unroll
-            for (int f = 0; f < F; f++)
-                dft_r<Ra1, -1>(v[f]);
+                for (int f = 0; f < F; f++)
+                    dft_r<Ra1, -1>(v[f]);
+            }
             return true;
         };
         auto store = [&](int u, V (&v)[F][Ra1]) {
             int b, j;
             dec(u, b, j);
+            if constexpr (mode == 5) {
+                // time domain, back where the values came from
+                V *dst = IP ? X : S;
 #pragma unroll
-            for (int f = 0; f < F; f++)
+                for (int f = 0; f < F; f++)
 #pragma unroll
-                for (int r = 0; r < Ra1; r++)
-                    X[CI(f, j * Ra1 + r, b)] = v[f][r];
+                    for (int r = 0; r < Ra1; r++)
+                        dst[CI(f, j + r * Ra2, b)] = v[f][r];
+            } else {
+#pragma unroll
+                for (int f = 0; f < F; f++)
+#pragma unroll
+                    for (int r = 0; r < Ra1; r++)
+                        X[CI(f, j * Ra1 + r, b)] = v[f][r];
+            }
         };
         if constexpr (IP && mode != 0) {
             // in place on X: a column's reads and writes stay within one warp
@@ -479,8 +528,10 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     };
 
     // ---- block B: forward row stage 2, spectral factor, inverse row stage 1
-    auto block_b = [&](bool cav, double *acc) {
+    auto block_b = [&](bool cav, double *acc, int kc) {
         const int items = F * Pc * Rb1;
+        const V *Dk = sCry[kc].D; // dispersion factors of crystal kc
+        const bool dsm = disp_smem && kc == 0;
         const V *src = IP ? Y : S;
         auto decode = [&](int u, int &j, int &row, int &f) {
             j = u & (Rb1 - 1);
@@ -504,7 +555,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
             // transform so that their latency overlaps it
             V fac[IP ? Rb2 : 1];
             if constexpr (IP) {
-                const V *tab = (cav ? gGt : gDt) + f * N + (k1 << LQ) + j;
+                const V *tab = (cav ? gGt : Dk) + f * N + (k1 << LQ) + j;
 #pragma unroll
                 for (int r = 0; r < Rb2; r++)
                     fac[r] = tab[r * Rb1];
@@ -521,7 +572,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
                 if constexpr (IP)
                     d = fac[r];
                 else
-                    d = cav ? gG[f * N + k] : (disp_smem ? Dsm[f * NC + (row << LQ) + k2] : gD[f * N + k]);
+                    d = cav ? gG[f * N + k] : (dsm ? Dsm[f * NC + (row << LQ) + k2] : Dk[f * N + k]);
                 if (cav && f == 1 && own) {
                     double p2 = (double)cabs2(v[r]);
                     acc[3] += p2;
@@ -651,13 +702,13 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     };
 
     // forward transform (after block A), frequency visit, inverse up to S
-    auto middle = [&](bool cav, double *acc) {
+    auto middle = [&](bool cav, double *acc, int kc) {
         __syncthreads();
         phase2();
         cluster.sync();
         phase3();
         __syncthreads();
-        block_b(cav, acc);
+        block_b(cav, acc, kc);
         __syncthreads();
         phase5();
         cluster.sync();
@@ -669,21 +720,39 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
     using M1 = std::integral_constant<int, 1>;
     using M2 = std::integral_constant<int, 2>;
     using M3 = std::integral_constant<int, 3>;
+    using M5 = std::integral_constant<int, 5>;
+    using M6 = std::integral_constant<int, 6>;
     cluster.sync(); // every CTA of the cluster is running; tables loaded
     double dummy[kNslot] = {0, 0, 0, 0, 0};
     // mode 0 enters round trip m_start + r_base (its m_cav is the one before)
+    set_crystal(0);
     block_a(M0{}, 0, 0, m_start + r_base - 1, true, false, dummy);
     for (int r = 0; r < M; r++) {
         const int64_t slot = (int64_t)r_base + r;
         const int64_t m = m_start + slot;
-        for (int jz = 0; jz + 1 < nz; jz++) {
-            middle(false, dummy);
-            block_a(M1{}, 4 * jz + 2, 4 * (jz + 1), 0, true, false, dummy);
+        // the z-steps of every crystal in order (step jz of crystal kc); at a
+        // boundary between two steps block A finishes one and starts the
+        // next, possibly in the next crystal (z restarts there: its stage
+        // factors from q = 0).  Few live registers: the crystal's step count
+        // is re-read from shared memory.
+        int jz = 0;
+        while (kcur + 1 < ncry || jz + 1 < sCry[kcur].nz) {
+            middle(false, dummy, kcur);
+            if (jz + 1 < sCry[kcur].nz) {
+                block_a(M1{}, 4 * jz + 2, 4 * (jz + 1), 0, true, false, dummy);
+                jz++;
+            } else {
+                block_a(M5{}, 4 * jz + 2, 0, 0, true, false, dummy);
+                set_crystal(kcur + 1);
+                __syncthreads();
+                block_a(M6{}, 0, 0, 0, true, false, dummy);
+                jz = 0;
+            }
         }
-        middle(false, dummy);
+        middle(false, dummy, kcur);
         double acc[kNslot] = {0, 0, 0, 0, 0};
-        block_a(M2{}, 4 * (nz - 1) + 2, 0, 0, true, write_out && r == M - 1, acc);
-        middle(true, acc);
+        block_a(M2{}, 4 * jz + 2, 0, 0, true, write_out && r == M - 1, acc);
+        middle(true, acc, 0);
         block_reduce5(acc, red);
         if (threadIdx.x == 0) {
             double *o = obs + (slot * C + c) * kNslot;
@@ -692,6 +761,7 @@ __global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
             if (!isfinite(acc[0] + acc[1] + acc[2]))
                 atomicOr(err, 1);
         }
+        set_crystal(0);
         block_a(M3{}, 0, 0, m, r + 1 < M, false, dummy);
     }
 }

@@ -31,6 +31,8 @@ struct InstDesc {
     NsPump ns;         // ns-pulsed pump (ns.on), replaces the pump table
     int kerr;          // chi(3) terms on
     double kerr_g[9];  // their coefficients G_xy, row-major
+    const CryDesc *cry; // every crystal of the round trip (cry[0]: the fields above)
+    int ncry;
 };
 
 // Observables of every instance and slot of the call: output power

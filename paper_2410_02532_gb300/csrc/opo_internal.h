@@ -39,6 +39,25 @@ struct Derived {
     NsPump ns;           // ns-pulsed pump parameters (ns.on = 0: pump table)
 };
 
+constexpr int kMaxCry = OPO_MAX_CRYSTALS;
+
+// Device-side description of one crystal of an instance's round trip.
+struct CryDesc {
+    const void *disp;   // F*N dispersion factors / N, natural order
+    const void *disp_t; // the same, row-major over N = P Q
+    const void *ekz;    // 4 nz + 1 factors e^{i dk q dz/4}
+    double kappa[3], h; // 2 pi d_eff / (n lambda); RK4 half step dz/2
+    int nz, use_dk, kerr;
+    double kerr_g[9];   // Kerr coefficients G_xy, row-major
+};
+
+// Tables of a crystal after the first (the first one's live in the
+// context's d_disp, d_disp_t and d_ekz).
+struct CrystalState {
+    void *disp = nullptr, *disp_t = nullptr, *ekz = nullptr;
+    int ekz_cap = 0;
+};
+
 struct FusedCfg {
     int kernel = 1;      // 1: generic, 2: size-specialised, 3: size-specialised in place
     bool kerr = false;   // instances carry the chi(3) terms (kernels 2, 3 instantiate it)
@@ -53,7 +72,13 @@ struct FusedCfg {
 
 struct opo_ctx {
     opo_grid grid;
-    opo_crystal crystal;
+    opo_crystal crystal;                  // the first crystal (== cry[0])
+    opo_crystal cry[OPO_MAX_CRYSTALS];    // every crystal of the round trip
+    int ncry = 1;
+    opo::CrystalState xs[OPO_MAX_CRYSTALS]; // tables of crystals 1..ncry-1
+    opo::CryDesc h_cry[OPO_MAX_CRYSTALS]; // host copy of the descriptors
+    opo::CryDesc *d_cry = nullptr;        // their device copy (kMaxCry entries)
+    bool kerr_any = false;                // some crystal has Kerr terms
     opo_cavity cavity;
     bool have_crystal = false, have_cavity = false;
     int device = 0;
@@ -99,6 +124,7 @@ namespace opo {
 
 // opo_setup.cu
 int setup_twiddles(opo_ctx *c);
+// tables of every crystal and the device copy of their descriptors
 int setup_crystal_tables(opo_ctx *c);
 int setup_cavity_tables(opo_ctx *c);
 int finalize_trace(opo_ctx *c, int64_t M, int parts);

@@ -337,26 +337,31 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
     PlainFFT<T> fft;
     fft.init(c);
     const Derived &d = c->dv;
-    const T h = (T)d.h;
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
     k_entry<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_pump, n, F, c->cavity.resonant_mask,
                                           c->dv.ns, c->d_ctl);
-    const V *ekz = (const V *)c->d_ekz;
-    for (int j = 0; j < c->crystal.nz; j++) {
-        for (int half = 0; half < 2; half++) {
-            int q0 = 4 * j + 2 * half;
-            if (F == 3)
-                k_rk4<T, 3><<<gN, kThreads, 0, st>>>(fld, n, ekz, q0, h, (T)d.kappa[0],
-                                                     (T)d.kappa[1], (T)d.kappa[2], d.use_dk,
-                                                     d.kerr, kerr_g<T>(d.kerr_g));
-            else
-                k_rk4<T, 2><<<gN, kThreads, 0, st>>>(fld, n, ekz, q0, h, (T)d.kappa[0],
-                                                     (T)d.kappa[1], (T)d.kappa[2], d.use_dk,
-                                                     d.kerr, kerr_g<T>(d.kerr_g));
-            if (half == 0) {
-                fft.template run<-1>(fld, scr, F, st);
-                k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_disp, F * n);
-                fft.template run<1>(fld, scr, F, st);
+    // every crystal in order; z of the e^{i dk z} factor restarts in each
+    for (int i = 0; i < c->ncry; i++) {
+        const CryDesc &cd = c->h_cry[i];
+        const V *ekz = (const V *)cd.ekz;
+        const T hc = (T)cd.h;
+        const KerrG<T> G = kerr_g<T>(cd.kerr_g);
+        for (int j = 0; j < cd.nz; j++) {
+            for (int half = 0; half < 2; half++) {
+                int q0 = 4 * j + 2 * half;
+                if (F == 3)
+                    k_rk4<T, 3><<<gN, kThreads, 0, st>>>(fld, n, ekz, q0, hc, (T)cd.kappa[0],
+                                                         (T)cd.kappa[1], (T)cd.kappa[2],
+                                                         cd.use_dk != 0, cd.kerr != 0, G);
+                else
+                    k_rk4<T, 2><<<gN, kThreads, 0, st>>>(fld, n, ekz, q0, hc, (T)cd.kappa[0],
+                                                         (T)cd.kappa[1], (T)cd.kappa[2],
+                                                         cd.use_dk != 0, cd.kerr != 0, G);
+                if (half == 0) {
+                    fft.template run<-1>(fld, scr, F, st);
+                    k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)cd.disp, F * n);
+                    fft.template run<1>(fld, scr, F, st);
+                }
             }
         }
     }

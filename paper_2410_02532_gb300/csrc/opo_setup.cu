@@ -166,9 +166,10 @@ bool kerr_coefficients(const opo_crystal &k, int F, double g[9])
     return on;
 }
 
-int setup_crystal_tables(opo_ctx *c)
+namespace {
+
+int crystal_tables(opo_ctx *c, const opo_crystal &k, void *disp, void *disp_t, void *ekz)
 {
-    const opo_crystal &k = c->crystal;
     DispArgs a;
     for (int x = 0; x < 3; x++) {
         a.alpha[x] = k.alpha_per_m[x];
@@ -183,16 +184,38 @@ int setup_crystal_tables(opo_ctx *c)
     int cnt = 4 * k.nz + 1;
     if (c->prec == OPO_FP64) {
         k_disp_table<double><<<grid_for((int64_t)c->F * c->n), 256, 0, c->stream>>>(
-            (double2 *)c->d_disp, (double2 *)c->d_disp_t, c->logn / 2, c->n, c->F, a);
-        k_ekz_table<double><<<grid_for(cnt), 256, 0, c->stream>>>((double2 *)c->d_ekz, cnt,
+            (double2 *)disp, (double2 *)disp_t, c->logn / 2, c->n, c->F, a);
+        k_ekz_table<double><<<grid_for(cnt), 256, 0, c->stream>>>((double2 *)ekz, cnt,
                                                                    k.dk_per_m, a.dz);
     } else {
         k_disp_table<float><<<grid_for((int64_t)c->F * c->n), 256, 0, c->stream>>>(
-            (float2 *)c->d_disp, (float2 *)c->d_disp_t, c->logn / 2, c->n, c->F, a);
-        k_ekz_table<float><<<grid_for(cnt), 256, 0, c->stream>>>((float2 *)c->d_ekz, cnt,
+            (float2 *)disp, (float2 *)disp_t, c->logn / 2, c->n, c->F, a);
+        k_ekz_table<float><<<grid_for(cnt), 256, 0, c->stream>>>((float2 *)ekz, cnt,
                                                                   k.dk_per_m, a.dz);
     }
     return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
+}
+
+} // namespace
+
+int setup_crystal_tables(opo_ctx *c)
+{
+    for (int i = 0; i < c->ncry; i++) {
+        void *disp = i == 0 ? c->d_disp : c->xs[i].disp;
+        void *disp_t = i == 0 ? c->d_disp_t : c->xs[i].disp_t;
+        void *ekz = i == 0 ? c->d_ekz : c->xs[i].ekz;
+        int rc = crystal_tables(c, c->cry[i], disp, disp_t, ekz);
+        if (rc != OPO_OK)
+            return rc;
+        c->h_cry[i].disp = disp;
+        c->h_cry[i].disp_t = disp_t;
+        c->h_cry[i].ekz = ekz;
+    }
+    // the pageable source is staged before cudaMemcpyAsync returns
+    if (cudaMemcpyAsync(c->d_cry, c->h_cry, sizeof(CryDesc) * c->ncry, cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess)
+        return OPO_E_CUDA;
+    return OPO_OK;
 }
 
 int setup_cavity_tables(opo_ctx *c)

@@ -71,6 +71,7 @@ _DP = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "opo_create": ([ctypes.POINTER(_P), ctypes.POINTER(Grid)], ctypes.c_int),
     "opo_set_crystal": ([_P, ctypes.POINTER(Crystal)], ctypes.c_int),
+    "opo_set_crystals": ([_P, ctypes.POINTER(Crystal), ctypes.c_int32], ctypes.c_int),
     "opo_set_cavity": ([_P, ctypes.POINTER(Cavity)], ctypes.c_int),
     "opo_set_fields": ([_P, ctypes.c_int32, _DP, ctypes.c_size_t, ctypes.c_int64], ctypes.c_int),
     "opo_run_roundtrips": ([_P, ctypes.c_int64, ctypes.POINTER(Stats)], ctypes.c_int),
@@ -139,6 +140,11 @@ def opo_create(grid: Grid):
 
 def opo_set_crystal(ctx, crystal: Crystal):
     _check(lib().opo_set_crystal(ctx, ctypes.byref(crystal)), "opo_set_crystal")
+
+
+def opo_set_crystals(ctx, crystals):
+    arr = (Crystal * len(crystals))(*crystals)
+    _check(lib().opo_set_crystals(ctx, arr, len(crystals)), "opo_set_crystals")
 
 
 def opo_set_cavity(ctx, cavity: Cavity):
@@ -227,6 +233,28 @@ def grid_from(cfg, precision=OPO_FP32_PH64, device=0, stream=None) -> Grid:
                 stream)
 
 
+def crystals_from(cfg, tod_div=0.0) -> list:
+    """The configuration's crystal followed by its ``extra_crystals`` (objects
+    with length, nz, dk, deff, nidx, alpha, dbeta1, beta2, beta3, beta4, n2;
+    wavelengths and waist are the configuration's)."""
+    out = [crystal_from(cfg, tod_div)]
+    for x in getattr(cfg, "extra_crystals", ()):
+        c = crystal_from(cfg, tod_div)
+        c.length_m = x.length
+        c.nz = x.nz
+        c.dk_per_m = x.dk
+        c.deff_mpv = x.deff
+        c.n = _D3(*x.nidx)
+        c.alpha_per_m = _D3(*x.alpha)
+        c.dbeta1_s_per_m = _D3(*x.dbeta1)
+        c.beta2_s2_per_m = _D3(*x.beta2)
+        c.beta3_s3_per_m = _D3(*x.beta3)
+        c.beta4_s4_per_m = _D3(*x.beta4)
+        c.n2_m2_per_W = x.n2
+        out.append(c)
+    return out
+
+
 def crystal_from(cfg, tod_div=0.0) -> Crystal:
     c = Crystal()
     c.length_m = cfg.length
@@ -279,7 +307,7 @@ class Context:
         self.precision = precision
         self.h = opo_create(grid_from(cfg, precision, device, stream))
         try:
-            opo_set_crystal(self.h, crystal_from(cfg, tod_div))
+            opo_set_crystals(self.h, crystals_from(cfg, tod_div))
             cav, keep = cavity_from(cfg, pump_user)
             opo_set_cavity(self.h, cav)
             del keep
@@ -297,7 +325,7 @@ class Context:
         if int(cfg.n) != self.n or int(cfg.nfields) != self.nfields:
             raise ValueError("reset needs the same N and field count")
         self.cfg = cfg
-        opo_set_crystal(self.h, crystal_from(cfg, tod_div))
+        opo_set_crystals(self.h, crystals_from(cfg, tod_div))
         cav, keep = cavity_from(cfg, pump_user)
         opo_set_cavity(self.h, cav)
         del keep

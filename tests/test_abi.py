@@ -65,6 +65,7 @@ def test_null_arguments(L):
     h = ctypes.c_void_p()
     assert L.opo_create(ctypes.byref(h), None) == opo.OPO_E_INVALID
     assert L.opo_set_crystal(None, None) == opo.OPO_E_INVALID
+    assert L.opo_set_crystals(None, None, 1) == opo.OPO_E_INVALID
     assert L.opo_run_roundtrips(None, 1, None) == opo.OPO_E_INVALID
     assert L.opo_destroy(None) == opo.OPO_OK
     assert L.opo_batch_create(None, None, 0, 0, 0) == opo.OPO_E_INVALID

@@ -1,0 +1,192 @@
+"""GPU parity with several crystals per round trip (the crystals passed in
+order, fields carried over, z restarting in each): every path against the
+oracle from the same stored state, the step sequence across launch and
+crystal boundaries, batches mixing crystal counts, and the identity that a
+crystal cut into two equal halves is the whole crystal (dk = 0).
+FP64 <= 1e-10, FP32 fields with FP64 phases <= 1e-4 relative L2 per field.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2410_02532_gb300 import opo
+from paper_2410_02532_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {opo.OPO_FP64: 1e-10, opo.OPO_FP32_PH64: 1e-4}
+PRECS = [opo.OPO_FP64, opo.OPO_FP32_PH64]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2410_02532_gb300 import build
+    build.build()
+    opo.lib()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_rt(cfg, fields, m0=0, M=1):
+    p = orc.params(cfg)
+    pump = orc.pump_profile(p, cfg.pump_kind if cfg.pump_kind < 2 else 0, cfg.pump_power,
+                            cfg.pump_fwhm)
+    out, trace, outf, st = orc.run(p, fields, pump, m0, M)
+    assert st == 0
+    return out, outf, trace
+
+
+def gpu_rt(cfg, fields, prec, path, cluster=0, m0=0, M=1, rtpl=0):
+    with opo.Context(cfg, precision=prec, fields=fields) as ctx:
+        ctx.set_fields(fields, rt_index=m0)
+        ctx.set_path(path, cluster, rtpl)
+        s = ctx.run(M)
+        return ctx.get_fields(), ctx.get_fields(opo.OPO_OUTPUT), ctx.trace(M), s
+
+
+def start(cfg, amp=2e6, seed_off=0):
+    a = cfg.initial_fields()
+    for x in range(1, cfg.nfields):
+        a[x] = a[x] + W.noise(cfg.n, amp, cfg.seed + 41 + seed_off, cfg.instance, x)
+    return a
+
+
+def three_crystals(n=1024, nz=(6, 4, 5), F=3, kerr=False):
+    """A dispersive SRO crystal followed by two more: a shorter one with the
+    opposite phase mismatch and d_eff sign and other indices, and a lossy one
+    with other dispersion (and Kerr terms when asked)."""
+    if F == 3:
+        base = W.cw_sro_16k().replace(n=n, nz=nz[0], length=8e-3, dk=90.0, name="three")
+    else:
+        base = W.degenerate_2field(n=n, level=3.0).replace(nz=nz[0], length=8e-3, dk=60.0)
+    c2 = W.Crystal(length=4e-3, nz=nz[1], dk=-150.0, deff=-18e-12,
+                   nidx=(base.nidx[0] * 1.01, base.nidx[1] * 1.02, base.nidx[2] * 1.01),
+                   dbeta1=(5e-11, 0.0, -2e-11), beta2=(2e-25, 3e-25, -1e-25))
+    c3 = W.Crystal(length=6e-3, nz=nz[2], dk=40.0, deff=10e-12, nidx=base.nidx,
+                   alpha=(2.0, 1.0, 3.0), beta3=(1e-39, -2e-39, 3e-39),
+                   n2=(2e-18 if kerr else 0.0), beta4=((1e-55, 0.0, 2e-55) if kerr else (0, 0, 0)))
+    return base.replace(extra_crystals=(c2, c3))
+
+
+CASES = [
+    ("plain_1024", lambda: three_crystals(1024), opo.OPO_PATH_PLAIN, 0),
+    ("generic_1024", lambda: three_crystals(1024), opo.OPO_PATH_FUSED, 0),
+    ("generic_512_2field", lambda: three_crystals(512, F=2), opo.OPO_PATH_FUSED, 0),
+    ("generic_1024_kerr", lambda: three_crystals(1024, kerr=True), opo.OPO_PATH_FUSED, 0),
+    ("three_buffer_4096", lambda: three_crystals(4096, (3, 2, 2)), opo.OPO_PATH_FUSED, 0),
+    ("three_buffer_8192_2field", lambda: three_crystals(8192, (2, 2, 1), F=2),
+     opo.OPO_PATH_FUSED, 0),
+    ("in_place_16384_c4", lambda: three_crystals(16384, (2, 1, 2)), opo.OPO_PATH_FUSED, 4),
+    ("in_place_16384_c4_kerr", lambda: three_crystals(16384, (2, 1, 2), kerr=True),
+     opo.OPO_PATH_FUSED, 4),
+    ("in_place_32768_c8", lambda: three_crystals(32768, (1, 1, 1)), opo.OPO_PATH_FUSED, 8),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=["fp64", "fp32ph64"])
+@pytest.mark.parametrize("name,make,path,cluster", CASES, ids=[c[0] for c in CASES])
+def test_round_trip(name, make, path, cluster, prec):
+    cfg = make()
+    a0 = start(cfg)
+    ref = oracle_rt(cfg, a0, m0=3)
+    try:
+        got = gpu_rt(cfg, a0, prec, path, cluster=cluster, m0=3)
+    except opo.OPOError as e:  # FP64 at 2^15 does not fit these clusters
+        assert e.status == opo.OPO_E_UNSUPPORTED and prec == opo.OPO_FP64
+        return
+    tol = TOL[prec]
+    for x in range(cfg.nfields):
+        assert rel_l2(got[0][x], ref[0][x]) <= tol, (name, "field", x)
+        assert rel_l2(got[1][x], ref[1][x]) <= tol, (name, "output", x)
+        assert abs(got[2][0, x] - ref[2][0, x]) <= 4 * tol * abs(ref[2][0, x]) + 1e-300
+    # the extra crystals matter: the first crystal alone gives another result
+    one = oracle_rt(cfg.replace(extra_crystals=()), a0, m0=3)
+    assert rel_l2(one[0][1], ref[0][1]) > 100 * tol
+
+
+@pytest.mark.parametrize("path,cluster,rtpl", [(opo.OPO_PATH_PLAIN, 0, 0),
+                                               (opo.OPO_PATH_FUSED, 0, 2),
+                                               (opo.OPO_PATH_FUSED, 8, 2)])
+def test_per_round_trip_chain(path, cluster, rtpl):
+    """Five round trips in one call across launch boundaries, each against the
+    oracle from the GPU's own previous state; one call equals calls of one."""
+    cfg = three_crystals(16384 if cluster else 2048, (2, 1, 2))
+    a = start(cfg)
+    M = 5
+    states = [a]
+    with opo.Context(cfg, precision=opo.OPO_FP64, fields=a) as ctx:
+        ctx.set_path(path, cluster, rtpl)
+        for _ in range(M):
+            ctx.run(1)
+            states.append(ctx.get_fields())
+    with opo.Context(cfg, precision=opo.OPO_FP64, fields=a) as ctx:
+        ctx.set_path(path, cluster, rtpl)
+        ctx.run(M)
+        assert np.array_equal(ctx.get_fields(), states[-1])
+    for r in range(M):
+        ref, _, _ = oracle_rt(cfg, states[r], m0=r)
+        for x in range(cfg.nfields):
+            assert rel_l2(states[r + 1][x], ref[x]) <= 1e-10, (r, x)
+
+
+@pytest.mark.parametrize("n,cluster", [(1024, 0), (4096, 0), (16384, 4), (16384, 8)])
+def test_split_crystal_is_the_whole_bitwise(n, cluster):
+    """dk = 0: two equal halves (z restarting in the second) run exactly the
+    step sequence of the whole crystal, so the results agree bit for bit on
+    every path (the specialised kernels end a crystal in two passes; the
+    complex products' multiply-adds are written out so that both compiled
+    copies round alike)."""
+    whole = W.cw_sro_16k().replace(n=n, nz=6, length=12e-3, alpha=(0.3, 0.2, 0.1))
+    half = whole.replace(length=6e-3, nz=3)
+    split = half.replace(extra_crystals=(W.Crystal(
+        length=6e-3, nz=3, dk=0.0, deff=half.deff, nidx=half.nidx, alpha=half.alpha,
+        dbeta1=half.dbeta1, beta2=half.beta2, beta3=half.beta3),))
+    a = start(whole)
+    for path in (opo.OPO_PATH_PLAIN, opo.OPO_PATH_FUSED):
+        if path == opo.OPO_PATH_PLAIN and cluster:
+            continue
+        r1 = gpu_rt(whole, a, opo.OPO_FP32_PH64, path, cluster=cluster, M=2)
+        r2 = gpu_rt(split, a, opo.OPO_FP32_PH64, path, cluster=cluster, M=2)
+        assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[2], r2[2])
+
+
+def test_batch_mixing_crystal_counts_is_bitwise():
+    base = W.cw_sro_16k().replace(n=4096, nz=3)
+    cfgs = [base, three_crystals(4096, (3, 2, 2)),
+            base.replace(extra_crystals=(W.Crystal(length=3e-3, nz=2, dk=20.0),)),
+            three_crystals(4096, (1, 3, 1), kerr=True)]
+    starts = [start(c, seed_off=i) for i, c in enumerate(cfgs)]
+    alone = []
+    for c, a in zip(cfgs, starts):
+        with opo.Context(c, fields=a) as ctx:
+            ctx.set_path(opo.OPO_PATH_FUSED, 2, 2)
+            ctx.run(3)
+            alone.append((ctx.get_fields(), ctx.trace(3)))
+    ctxs = [opo.Context(c, fields=a) for c, a in zip(cfgs, starts)]
+    try:
+        b = opo.opo_batch_create([c.h for c in ctxs], 2)
+        opo.opo_batch_run(b, 3)
+        for ctx, (f, t) in zip(ctxs, alone):
+            assert np.array_equal(ctx.get_fields(), f)
+            assert np.array_equal(ctx.trace(3), t)
+        opo.opo_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_set_crystals_validation():
+    cfg = three_crystals(256, (2, 2, 2))
+    with opo.Context(cfg) as ctx:
+        cr = opo.crystals_from(cfg)
+        bad = opo.crystals_from(cfg)
+        bad[1].lambda_m = opo._D3(1.0e-6, 1.5e-6, 3.0e-6)  # other fields
+        for arr, cnt in ((cr, 0), (cr * 3, 9)):
+            a = (opo.Crystal * max(1, len(arr)))(*arr)
+            assert opo.lib().opo_set_crystals(ctx.h, a, cnt) == opo.OPO_E_INVALID
+        a = (opo.Crystal * 3)(*bad)
+        assert opo.lib().opo_set_crystals(ctx.h, a, 3) == opo.OPO_E_INVALID
+        # the context still runs its old crystals
+        ctx.run(1)
