@@ -25,7 +25,7 @@ int dispatch(int op, bool ip, bool kr, bool dbl, int F, int logn, const InstDesc
 // In-place variant: X and Y only, dispersion factors from L2.
 bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
-    if (logn != 14 && logn != 15)
+    if (logn < 14 || logn > 16 || (logn == 16 && dbl))
         return false;
     const int LP = logn / 2, LQ = logn - LP;
     if ((1 << LP) < C || (1 << LQ) < C)
@@ -33,7 +33,7 @@ bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, Fused
     const int A2 = (LP + 1) / 2, A1 = LP - A2;
     const int Qc = (1 << LQ) / C;
     const int nc = (1 << logn) / C;
-    const int maxT = dbl ? 256 : 512;
+    const int maxT = (dbl || logn >= 16) ? 256 : 512;
     int threads = threads_req;
     if (threads == 0)
         threads = std::min(maxT, (F * Qc * (1 << A1) + 31) / 32 * 32);
@@ -73,7 +73,7 @@ bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_
     const int Qc = (1 << LQ) / C, Pc = (1 << LP) / C;
     const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
     const int LS = (logn + 1) / 2;
-    const int maxT = dbl ? 256 : 384;
+    const int maxT = (dbl || logn >= 16) ? 256 : 384;
     // default: one work item per thread in the column phases (2 and 6);
     // the row phases may take two rounds
     int items = F * Qc * (1 << A1);
@@ -111,7 +111,7 @@ bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_
 // memory.
 bool fused2_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
-    if (logn < 12 || logn > 15)
+    if (logn < 12 || logn > 16 || (logn == 16 && dbl))
         return false;
     FusedCfg a, b;
     const bool ok_a = three_buffer_config(dbl, kr, F, logn, C, threads_req, &a);

@@ -1,7 +1,8 @@
 #pragma once
 // opo_fused2.cuh -- fused round-trip kernel specialised at compile time for
-// N = P Q with P = 2^LP in {64, 128}, Q = 2^LQ in {64, 128, 256} (N = 2^12 ...
-// 2^15), field count F and precision.  Same method, layout and cluster
+// N = P Q with P = 2^LP in {64, 128, 256}, Q = 2^LQ in {64, 128, 256}
+// (N = 2^12 ... 2^16; 2^16 in single precision only), field count F and
+// precision.  Same method, layout and cluster
 // exchange as the generic fused kernel (opo_fused.cu: time domain columns in
 // X, frequency-domain rows in Y, two cluster barriers per z-step), with every
 // transform split into exactly two Stockham stages whose radices mirror
@@ -71,11 +72,15 @@ __device__ __forceinline__ void dft_r(V *v)
 
 template <class T, bool IP>
 constexpr int kF2MaxThreads = IP ? F2IpTraits<T>::kMaxThreads : F2Traits<T>::kMaxThreads;
+// P = 256 (N = 2^16): a block-A item holds 16 values per field, which needs
+// more than 128 registers: at most 256 threads
+template <class T, bool IP, int LP>
+constexpr int kF2MaxThreadsL = LP >= 8 ? 256 : kF2MaxThreads<T, IP>;
 
 // KR: the Kerr (chi(3)) terms are part of the nonlinear step (a separate
 // instantiation, so that the chi(2)-only kernel keeps its registers and code)
 template <class T, int F, int LP, int LQ, bool IP, bool KR>
-__global__ void __launch_bounds__(kF2MaxThreads<T, IP>, 1)
+__global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     k_fused2(const InstDesc *__restrict__ descs, int r_base, int M, int write_out, int disp_smem)
 {
     using V = cv<T>;
@@ -848,6 +853,11 @@ OPO_F2_DISPATCH_KR_DECL(dispatch_f64_f2_kerr);
             OPO_F2_ONE(T, F, 7, 7, true, KR);                                                    \
         case 15:                                                                                 \
             OPO_F2_ONE(T, F, 7, 8, true, KR);                                                    \
+        case 16:                                                                                 \
+            if constexpr (sizeof(T) == 4) {                                                      \
+                OPO_F2_ONE(T, F, 8, 8, true, KR);                                                \
+            }                                                                                    \
+            return op == 0 ? OPO_E_UNSUPPORTED : 0;                                              \
         default:                                                                                 \
             return op == 0 ? OPO_E_UNSUPPORTED : 0;                                              \
         }                                                                                        \
@@ -861,6 +871,11 @@ OPO_F2_DISPATCH_KR_DECL(dispatch_f64_f2_kerr);
         OPO_F2_ONE(T, F, 7, 7, false, KR);                                                       \
     case 15:                                                                                     \
         OPO_F2_ONE(T, F, 7, 8, false, KR);                                                       \
+    case 16:                                                                                     \
+        if constexpr (sizeof(T) == 4) {                                                          \
+            OPO_F2_ONE(T, F, 8, 8, false, KR);                                                   \
+        }                                                                                        \
+        return op == 0 ? OPO_E_UNSUPPORTED : 0;                                                  \
     default:                                                                                     \
         return op == 0 ? OPO_E_UNSUPPORTED : 0;                                                  \
     }

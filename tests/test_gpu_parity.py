@@ -413,3 +413,48 @@ def test_inplace_kernel_batch_and_resume_bitwise():
     finally:
         for c in ctxs:
             c.close()
+
+
+# -------------------------- N = 2^16: P = Q = 256, 16-CTA clusters (FP32)
+
+N16_CASES = [
+    ("sync_eom_delay_3f", lambda: W.sync_pumped_64k(delay_fs=15.0).replace(nz=4)),
+    ("degenerate_dk_2f", lambda: cfg_degenerate(n=1 << 16).replace(nz=4)),
+    ("dro_loss_dk_3f", lambda: cfg_dro(n=1 << 16).replace(nz=3)),
+]
+
+
+@pytest.mark.parametrize("name,make", N16_CASES, ids=[c[0] for c in N16_CASES])
+def test_fused_n65536(name, make):
+    """The 2^16-point size runs fused (one 16-CTA cluster per instance, 256
+    threads) and matches the oracle per pass."""
+    cfg = make()
+    a0 = strong(cfg, 1e6)
+    ref = oracle_rt(cfg, a0, m0=2)
+    got = gpu_rt(cfg, a0, opo.OPO_FP32_PH64, opo.OPO_PATH_FUSED, m0=2)
+    compare(cfg, got, ref, opo.OPO_FP32_PH64, name)
+    assert got[3].path == opo.OPO_PATH_FUSED and got[3].cluster == 16
+
+
+def test_fused_n65536_batch_resume_bitwise():
+    base = W.sync_pumped_64k(delay_fs=-10.0).replace(nz=3)
+    cfgs = [base, base.replace(pump_power=1.5 * base.pump_power, delay=5e-15)]
+    starts = [strong(c, 1e6, i) for i, c in enumerate(cfgs)]
+    alone = []
+    for c, a in zip(cfgs, starts):
+        with opo.Context(c, fields=a) as ctx:
+            ctx.set_path(opo.OPO_PATH_FUSED, 16, 2)
+            ctx.run(3)
+            alone.append((ctx.get_fields(), ctx.trace(3)))
+    ctxs = [opo.Context(c, fields=a) for c, a in zip(cfgs, starts)]
+    try:
+        b = opo.opo_batch_create([c.h for c in ctxs], 16)
+        opo.opo_batch_run(b, 1)
+        opo.opo_batch_run(b, 2)
+        for ctx, (f, t) in zip(ctxs, alone):
+            assert np.array_equal(ctx.get_fields(), f)
+            assert np.array_equal(ctx.trace(2), t[1:])
+        opo.opo_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            c.close()

@@ -26,7 +26,7 @@ def _requests():
         (mk(16384, pump_kind=W.PUMP_SECH2, pump_fwhm=1e-12, eom_beta=0.5, eom_f=10e9,
             delay=10e-15), 17, 0.02),
         (mk(4096, instance=7, pump_power=2 * base.pump_power), 50, 0.05),
-        (mk(65536), 6, 0.06),  # too large for the fused path: plain path
+        (mk(131072), 4, 0.06),  # too large for the fused path: plain path
     ]
     return [serving.Request(i, c.replace(instance=i), m, t) for i, (c, m, t) in enumerate(cfgs)]
 
