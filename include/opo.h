@@ -207,6 +207,22 @@ OPO_API int opo_run_roundtrips(opo_ctx *ctx, int64_t m, opo_stats *stats);
  * trip, zero before the first.  Synchronizes the stream. */
 OPO_API int opo_get_fields(opo_ctx *ctx, int32_t field, int32_t which, double *out, size_t n);
 
+/* Output history, the per-round-trip output vectors the paper saves (e.g.
+ * the output pump and signal of an ns pulse over its round trips, Sec. 4.2):
+ * with max_rt > 0 every following opo_run_roundtrips / opo_batch_run call
+ * records the output-coupled fields of each of its round trips, row r of the
+ * history holding round trip r of the call (F x N complex values in the
+ * context's precision, on the device).  max_rt = 0 frees the history.
+ * While it is on, a call with more than max_rt round trips returns
+ * OPO_E_INVALID.  OPO_E_NOMEM if the rows cannot be allocated. */
+OPO_API int opo_set_output_history(opo_ctx *ctx, int64_t max_rt);
+
+/* Copy rows [row0, row0 + rows) of field `field` of the output history into
+ * out (rows x 2N doubles, interleaved re/im).  OPO_E_STATE without a history;
+ * OPO_E_INVALID for rows outside it.  Synchronizes. */
+OPO_API int opo_get_output_history(opo_ctx *ctx, int32_t field, int64_t row0, int64_t rows,
+                                   double *out);
+
 /* Copy the per-round-trip observables of the last opo_run_roundtrips call:
  * rows {P_p_out, P_s_out, P_i_out, nu_c} [W, W, W, Hz], `rows` rows (at most
  * the call's M).  Synchronizes. */

@@ -101,6 +101,8 @@ void free_all(opo_ctx *c)
     }
     if (c->d_cry)
         cudaFree(c->d_cry);
+    if (c->d_hist)
+        cudaFree(c->d_hist);
     if (c->h_pinned)
         cudaFreeHost(c->h_pinned);
     if (c->graph)
@@ -615,9 +617,65 @@ int opo_set_path(opo_ctx *c, int32_t path, int32_t cluster, int32_t rt_per_launc
     return OPO_OK;
 }
 
+int opo_set_output_history(opo_ctx *c, int64_t max_rt)
+{
+    if (!c || max_rt < 0)
+        return OPO_E_INVALID;
+    const size_t row = c->csz * (size_t)c->F * c->n;
+    if (max_rt > (int64_t)(((size_t)1 << 38) / row)) // 256 GiB
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    cudaStreamSynchronize(c->stream);
+    if (c->d_hist)
+        cudaFree(c->d_hist);
+    c->d_hist = nullptr;
+    c->hist_cap = 0;
+    c->graph_valid = false;
+    if (max_rt == 0)
+        return OPO_OK;
+    if (cudaMalloc(&c->d_hist, row * (size_t)max_rt) != cudaSuccess) {
+        c->d_hist = nullptr;
+        cudaGetLastError();
+        return OPO_E_NOMEM;
+    }
+    c->hist_cap = max_rt;
+    return OPO_OK;
+}
+
+int opo_get_output_history(opo_ctx *c, int32_t field, int64_t row0, int64_t rows, double *out)
+{
+    if (!c || !out || field < 0 || field >= c->F || row0 < 0 || rows < 0)
+        return OPO_E_INVALID;
+    if (!c->d_hist)
+        return OPO_E_STATE;
+    if (row0 + rows > c->hist_cap)
+        return OPO_E_INVALID;
+    DeviceGuard g(c->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    for (int64_t r = 0; r < rows; r++) {
+        const char *src = (const char *)c->d_hist +
+                          ((size_t)(row0 + r) * c->F + field) * (size_t)c->n * c->csz;
+        if (c->prec == OPO_FP64)
+            k_to_f64<double><<<blocks(c->n), 256, 0, c->stream>>>(c->d_stage, (const double2 *)src, c->n);
+        else
+            k_to_f64<float><<<blocks(c->n), 256, 0, c->stream>>>(c->d_stage, (const float2 *)src, c->n);
+        if (cudaGetLastError() != cudaSuccess)
+            return OPO_E_CUDA;
+        if (cudaMemcpyAsync(out + (size_t)r * 2 * c->n, c->d_stage, sizeof(double) * 2 * c->n,
+                            cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            return OPO_E_CUDA;
+    }
+    return check_err(c);
+}
+
 int opo_run_roundtrips(opo_ctx *c, int64_t m, opo_stats *stats)
 {
     if (!c || m < 0)
+        return OPO_E_INVALID;
+    if (c->d_hist && m > c->hist_cap)
         return OPO_E_INVALID;
     if (!c->have_crystal || !c->have_cavity)
         return OPO_E_STATE;
@@ -847,6 +905,9 @@ int opo_batch_run(opo_batch *b, int64_t m)
 {
     if (!b || m < 0)
         return OPO_E_INVALID;
+    for (const opo_ctx *c : b->ctxs)
+        if (c->d_hist && m > c->hist_cap)
+            return OPO_E_INVALID;
     opo_ctx *c0 = b->ctxs[0];
     DeviceGuard g(c0->device);
     if (!g.ok)

@@ -318,6 +318,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             int f = i / NC;
             acc[f] += (double)cabs2(X[i]);
         }
+        if (d.hist) { // output history row of this round trip
+            V *row = (V *)d.hist + (size_t)slot * F * n;
+            for (int i = threadIdx.x; i < F * NC; i += blockDim.x) {
+                int f = i / NC;
+                row[(size_t)f * n + gindex(i - f * NC)] = cscale(X[i], (T)d.outscale[f]);
+            }
+        }
         if (write_out && r == M - 1) {
             V *go = (V *)d.out;
             for (int i = threadIdx.x; i < F * NC; i += blockDim.x) {
@@ -490,6 +497,7 @@ void fill_desc(InstDesc &d, const opo_ctx *c)
 {
     d.fields = c->d_fields;
     d.out = c->d_out;
+    d.hist = c->d_hist;
     d.pump = c->d_pump;
     d.disp = c->d_disp;
     d.gdd = c->d_gdd;

@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     const int64_t m_start = dg.m_start;
     V *gF = (V *)dg.fields;
     V *gOut = (V *)dg.out;
+    V *gHist = (V *)dg.hist;
     const V *gPump = (const V *)dg.pump;
     const V *gD = (const V *)dg.disp;
     const V *gG = (const V *)dg.gdd;
@@ -225,7 +226,8 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     // ---- block A: shared by every z-step boundary
     // mode 0: first round trip of the launch, input from global memory
     // mode 1: interior z-step boundary
-    // mode 2: end of the crystal pass (observables, then cavity forward)
+    // mode 2: end of the crystal pass (observables and outputs, with the
+    //         output history row m_cav, then cavity forward)
     // mode 3: end of the cavity visit of round trip m_cav (mirror, EOM, then
     //         entry of round trip m_cav + 1, or the final store)
     // modes 5 and 6: a z-step boundary where one crystal ends and the next
@@ -319,6 +321,11 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                             acc[f] += (double)cabs2(v[f][r]);
                         if (save_out && own)
                             gOut[f * N + gtime(j + r * Ra2, b)] = cmul(v[f][r], osc[f]);
+                        // output history: row m_cav (the round trip's slot in
+                        // the call) in mode 2
+                        if (gHist && own)
+                            gHist[(size_t)m_cav * F * N + f * N + gtime(j + r * Ra2, b)] =
+                                cmul(v[f][r], osc[f]);
                     }
                 }
             }
@@ -756,7 +763,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
         }
         middle(false, dummy, kcur);
         double acc[kNslot] = {0, 0, 0, 0, 0};
-        block_a(M2{}, 4 * jz + 2, 0, 0, true, write_out && r == M - 1, acc);
+        block_a(M2{}, 4 * jz + 2, 0, slot, true, write_out && r == M - 1, acc);
         middle(true, acc, 0);
         block_reduce5(acc, red);
         if (threadIdx.x == 0) {

@@ -10,6 +10,7 @@ namespace opo {
 struct InstDesc {
     void *fields;      // F*N state (read at start, written at end)
     void *out;         // F*N output-coupled fields of the last round trip
+    void *hist;        // output history rows [slot][F*N], or null
     const void *pump;  // N input pump
     const void *disp;  // F*N dispersion factors / N (natural order)
     const void *gdd;   // F*N cavity spectral factors / N (natural order)

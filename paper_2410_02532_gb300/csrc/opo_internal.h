@@ -104,6 +104,8 @@ struct opo_ctx {
     int ekz_cap = 0;
     double *d_pump_user = nullptr; // staging for OPO_PUMP_USER (FP64)
     double *d_stage = nullptr;     // 2N doubles: host <-> device field staging
+    void *d_hist = nullptr;    // output history: hist_cap rows of F*N (optional)
+    int64_t hist_cap = 0;
     double *d_obs = nullptr;   // raw observable sums
     double *d_trace = nullptr; // rows {P_p, P_s, P_i, nu_c}
     int64_t obs_cap = 0;       // capacity in round trips (times parts)

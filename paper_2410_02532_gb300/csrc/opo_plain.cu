@@ -222,11 +222,17 @@ __global__ void k_spec_sums(const cv<T> *spec, int n, DevCtl *ctl)
 }
 
 template <class T>
-__global__ void k_save_output(const cv<T> *fields, cv<T> *out, int n, int F, T s0, T s1, T s2)
+__global__ void k_save_output(const cv<T> *fields, cv<T> *out, int n, int F, T s0, T s1, T s2,
+                              cv<T> *hist, const DevCtl *ctl)
 {
     const T sc[3] = {s0, s1, s2};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F * n; i += gridDim.x * blockDim.x)
-        out[i] = cscale(fields[i], sc[i / n]);
+    cv<T> *row = hist ? hist + (size_t)ctl->slot * F * n : nullptr; // history row of this round trip
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F * n; i += gridDim.x * blockDim.x) {
+        const cv<T> o = cscale(fields[i], sc[i / n]);
+        out[i] = o;
+        if (row)
+            row[i] = o;
+    }
 }
 
 struct CavArgs {
@@ -367,7 +373,8 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
     }
     k_power_sums<T><<<F, 512, 0, st>>>(fld, n, c->d_ctl);
     k_save_output<T><<<gFN, kThreads, 0, st>>>(fld, (V *)c->d_out, n, F, (T)d.outscale[0],
-                                                (T)d.outscale[1], (T)d.outscale[2]);
+                                                (T)d.outscale[1], (T)d.outscale[2],
+                                                (V *)c->d_hist, c->d_ctl);
     // cavity spectral visit: every resonant field with GDD or delay, and the
     // signal for its spectral centroid
     bool need_all = false;

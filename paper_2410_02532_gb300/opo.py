@@ -77,6 +77,9 @@ _SIGS = {
     "opo_run_roundtrips": ([_P, ctypes.c_int64, ctypes.POINTER(Stats)], ctypes.c_int),
     "opo_get_fields": ([_P, ctypes.c_int32, ctypes.c_int32, _DP, ctypes.c_size_t], ctypes.c_int),
     "opo_get_trace": ([_P, _DP, ctypes.c_int64], ctypes.c_int),
+    "opo_set_output_history": ([_P, ctypes.c_int64], ctypes.c_int),
+    "opo_get_output_history": ([_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _DP],
+                               ctypes.c_int),
     "opo_set_fields_device": ([_P, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.c_int64],
                               ctypes.c_int),
     "opo_get_fields_device": ([_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t],
@@ -176,6 +179,17 @@ def opo_get_fields(ctx, field: int, which: int, n: int):
 def opo_get_trace(ctx, rows: int):
     out = np.empty((int(rows), 4), dtype=np.float64)
     _check(lib().opo_get_trace(ctx, out.ctypes.data_as(_DP), int(rows)), "opo_get_trace")
+    return out
+
+
+def opo_set_output_history(ctx, max_rt):
+    _check(lib().opo_set_output_history(ctx, int(max_rt)), "opo_set_output_history")
+
+
+def opo_get_output_history(ctx, field, row0, rows, n):
+    out = np.zeros((int(rows), int(n)), dtype=np.complex128)
+    _check(lib().opo_get_output_history(ctx, int(field), int(row0), int(rows),
+                                        out.ctypes.data_as(_DP)), "opo_get_output_history")
     return out
 
 
@@ -347,6 +361,17 @@ class Context:
 
     def trace(self, rows):
         return opo_get_trace(self.h, rows)
+
+    def set_history(self, max_rt):
+        """Record the output-coupled fields of every round trip of the next
+        calls (up to max_rt per call); 0 turns it off."""
+        opo_set_output_history(self.h, max_rt)
+
+    def history(self, rows, row0=0):
+        """(rows, F, N) complex output fields of round trips row0.. of the
+        last call."""
+        return np.stack([opo_get_output_history(self.h, x, row0, rows, self.n)
+                         for x in range(self.nfields)], axis=1)
 
     def sync(self):
         opo_sync(self.h)

@@ -305,3 +305,67 @@ def test_kerr_allocation_free_pass():
     got = dev.cpu().numpy()
     for x in range(cfg.nfields):
         assert rel_l2(got[x], ref[x]) <= 1e-10
+
+
+# ------------------------------------------- per-round-trip output history
+
+HIST_CASES = [
+    ("plain_ns_1024", lambda: cfg_ns2(n=1024, nz=6), opo.OPO_PATH_PLAIN, 0),
+    ("generic_ns_1024", lambda: cfg_ns2(n=1024, nz=6), opo.OPO_PATH_FUSED, 0),
+    ("three_buffer_tro_4096", lambda: cfg_tro(n=4096, nz=4), opo.OPO_PATH_FUSED, 0),
+    ("in_place_ns3_16384", lambda: cfg_ns3(n=16384, nz=3), opo.OPO_PATH_FUSED, 4),
+]
+
+
+@pytest.mark.parametrize("name,make,path,cluster", HIST_CASES, ids=[c[0] for c in HIST_CASES])
+def test_output_history(name, make, path, cluster):
+    """Row r of the history is the output of round trip r of the call: equal
+    to the output read after running the round trips one at a time, the last
+    row equal to the call's output fields, its power equal to the trace; the
+    first row against the oracle."""
+    cfg = make()
+    a = start(cfg, pump_amp=(4e5 if cfg.resonant_mask & 1 else 0.0))
+    M = 4
+    with opo.Context(cfg, precision=opo.OPO_FP32_PH64, fields=a) as ctx:
+        ctx.set_fields(a, rt_index=2)
+        ctx.set_path(path, cluster, 3)
+        ctx.set_history(M + 1)
+        ctx.run(M)
+        hist = ctx.history(M)
+        tr = ctx.trace(M)
+        assert np.array_equal(hist[-1], ctx.get_fields(opo.OPO_OUTPUT))
+        with pytest.raises(opo.OPOError) as ei:
+            ctx.run(M + 2)  # more round trips than rows
+        assert ei.value.status == opo.OPO_E_INVALID
+    steps = []
+    with opo.Context(cfg, precision=opo.OPO_FP32_PH64, fields=a) as ctx:
+        ctx.set_fields(a, rt_index=2)
+        ctx.set_path(path, cluster, 3)
+        for _ in range(M):
+            ctx.run(1)
+            steps.append(ctx.get_fields(opo.OPO_OUTPUT))
+    for r in range(M):
+        assert np.array_equal(hist[r], steps[r]), r
+    # the pump power of each row is the trace's output pump power
+    p = orc.params(cfg)
+    for r in range(M):
+        assert abs(orc.power(p, 0, hist[r, 0]) - tr[r, 0]) <= 1e-4 * tr[r, 0]
+    # and round trip 0 against the oracle
+    _, outf, _ = oracle_rt(cfg, a, m0=2)
+    for x in range(cfg.nfields):
+        assert rel_l2(hist[0, x], outf[x]) <= 1e-4
+
+
+def test_output_history_off_and_errors():
+    cfg = cfg_ns2(n=256, nz=2)
+    with opo.Context(cfg) as ctx:
+        with pytest.raises(opo.OPOError) as ei:
+            opo.opo_get_output_history(ctx.h, 0, 0, 1, cfg.n)
+        assert ei.value.status == opo.OPO_E_STATE
+        ctx.set_history(2)
+        ctx.run(2)
+        with pytest.raises(opo.OPOError) as ei:
+            opo.opo_get_output_history(ctx.h, 0, 1, 2, cfg.n)  # beyond the rows
+        assert ei.value.status == opo.OPO_E_INVALID
+        ctx.set_history(0)
+        ctx.run(5)  # no limit once off
