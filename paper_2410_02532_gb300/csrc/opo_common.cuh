@@ -58,28 +58,31 @@ template <class V> __device__ __forceinline__ typename cscal<V>::type cabs2(V a)
 }
 
 // ------------------------------------------------- in-register DFTs ----
-// DFT of R values in natural order, X_k = sum_j v_j e^{DIR 2 pi i jk/R},
-// DIR = -1 forward, +1 inverse (unnormalized).  Recursive even/odd split
-// (radix-2 decimation in time); the constant twiddles are e^{DIR 2 pi i a/16}.
+// DFT of R values in natural order (R = 1 .. 32), X_k = sum_j v_j
+// e^{DIR 2 pi i jk/R}, DIR = -1 forward, +1 inverse (unnormalized).
+// Recursive even/odd split (radix-2 decimation in time); the constant
+// twiddles are e^{DIR 2 pi i a/32}.
 
 template <int A, int DIR, class V>
-__device__ __forceinline__ V rot16(V x)
+__device__ __forceinline__ V rot32(V x)
 {
-    // cos and sin of 2 pi a / 16, a = 0..7 (mathematical constants)
-    constexpr double c16[8] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
-                               0.38268343236508977173, 0.0, -0.38268343236508977173,
-                               -0.70710678118654752440, -0.92387953251128675613};
-    constexpr double s16[8] = {0.0, 0.38268343236508977173, 0.70710678118654752440,
-                               0.92387953251128675613, 1.0, 0.92387953251128675613,
-                               0.70710678118654752440, 0.38268343236508977173};
+    // cos and sin of 2 pi a / 32, a = 0..15 (mathematical constants)
+    constexpr double c32[16] = {1.00000000000000000000, 0.980785280403230449126, 0.923879532511286756128, 0.831469612302545237079,
+                                0.707106781186547524401, 0.555570233019602224743, 0.382683432365089771728, 0.195090322016128267848,
+                                0.0, -0.195090322016128267848, -0.382683432365089771728, -0.555570233019602224743,
+                                -0.707106781186547524401, -0.831469612302545237079, -0.923879532511286756128, -0.980785280403230449126};
+    constexpr double s32[16] = {0.0, 0.195090322016128267848, 0.382683432365089771728, 0.555570233019602224743,
+                                0.707106781186547524401, 0.831469612302545237079, 0.923879532511286756128, 0.980785280403230449126,
+                                1.00000000000000000000, 0.980785280403230449126, 0.923879532511286756128, 0.831469612302545237079,
+                                0.707106781186547524401, 0.555570233019602224743, 0.382683432365089771728, 0.195090322016128267848};
     using S = typename cscal<V>::type;
     if constexpr (A == 0) {
         return x;
-    } else if constexpr (A == 4) {
+    } else if constexpr (A == 8) {
         return DIR < 0 ? cmk<V>(x.y, -x.x) : cmk<V>(-x.y, x.x);
     } else {
-        const S c = (S)c16[A];
-        const S s = (S)(DIR * s16[A]);
+        const S c = (S)c32[A];
+        const S s = (S)(DIR * s32[A]);
         return cmk<V>(fmad_(x.x, c, -(x.y * s)), fmad_(x.x, s, x.y * c));
     }
 }
@@ -88,7 +91,7 @@ template <int R, int DIR, int K, class V>
 __device__ __forceinline__ void dft_combine(V *v, const V *e, const V *o)
 {
     if constexpr (K < R / 2) {
-        V t = rot16<K * (16 / R), DIR>(o[K]);
+        V t = rot32<K * (32 / R), DIR>(o[K]);
         v[K] = cadd(e[K], t);
         v[K + R / 2] = csub(e[K], t);
         dft_combine<R, DIR, K + 1>(v, e, o);

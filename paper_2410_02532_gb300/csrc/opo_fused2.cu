@@ -30,13 +30,13 @@ bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, Fused
     const int LP = logn / 2, LQ = logn - LP;
     if ((1 << LP) < C || (1 << LQ) < C)
         return false;
-    const int A2 = (LP + 1) / 2, A1 = LP - A2;
+    const int A2 = f2::f2_col_a2(LP), A1 = LP - A2;
     const int Qc = (1 << LQ) / C;
     const int nc = (1 << logn) / C;
-    const int maxT = (dbl || logn >= 16) ? 256 : 512;
+    const int maxT = dbl ? 256 : (logn >= 16 ? 384 : 512);
     int threads = threads_req;
-    if (threads == 0)
-        threads = std::min(maxT, (F * Qc * (1 << A1) + 31) / 32 * 32);
+    if (threads == 0) // 2^16: 256 (two block-A items per thread) measured best
+        threads = logn >= 16 ? 256 : std::min(maxT, (F * Qc * (1 << A1) + 31) / 32 * 32);
     if (threads < 32 || threads > maxT || (threads & 31))
         return false;
     (void)A2;
@@ -67,17 +67,18 @@ bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_
     const int LP = logn / 2, LQ = logn - LP;
     if ((1 << LP) < C || (1 << LQ) < C)
         return false;
-    const int A1 = LP - (LP + 1) / 2;
+    const int A1 = LP - f2::f2_col_a2(LP);
     const int B1 = LQ - (LQ + 1) / 2, B2 = (LQ + 1) / 2;
     const int nc = (1 << logn) / C;
     const int Qc = (1 << LQ) / C, Pc = (1 << LP) / C;
     const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
     const int LS = (logn + 1) / 2;
-    const int maxT = (dbl || logn >= 16) ? 256 : 384;
+    const int maxT = dbl ? 256 : 384;
     // default: one work item per thread in the column phases (2 and 6);
     // the row phases may take two rounds
     int items = F * Qc * (1 << A1);
-    int threads = threads_req > 0 ? threads_req : std::min(maxT, ((items + 31) / 32) * 32);
+    int threads = threads_req > 0 ? threads_req
+                                  : (logn >= 16 ? 256 : std::min(maxT, ((items + 31) / 32) * 32));
     if (threads > maxT || threads < 32 || (threads & 31))
         return false;
     (void)B1;

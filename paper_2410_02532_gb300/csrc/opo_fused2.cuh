@@ -72,10 +72,17 @@ __device__ __forceinline__ void dft_r(V *v)
 
 template <class T, bool IP>
 constexpr int kF2MaxThreads = IP ? F2IpTraits<T>::kMaxThreads : F2Traits<T>::kMaxThreads;
-// P = 256 (N = 2^16): a block-A item holds 16 values per field, which needs
-// more than 128 registers: at most 256 threads
+// Column split [Ra1, Ra2] = [2^A1, 2^A2] of a P = 2^LP column transform:
+// A2 = ceil(LP/2), except P = 256, split [8, 32] so that a block-A item keeps
+// 8 values per field as at smaller sizes (a [16, 16] split put 16 RK4 points
+// of every field in one thread: 255 registers and block A at half speed);
+// the 32-point stages go to the column push and the last inverse stage.
+constexpr int f2_col_a2(int LP) { return LP == 8 ? 5 : (LP + 1) / 2; }
+
+// P = 256 (N = 2^16): the 32-point column stages need more than 128
+// registers: at most 384 threads
 template <class T, bool IP, int LP>
-constexpr int kF2MaxThreadsL = LP >= 8 ? 256 : kF2MaxThreads<T, IP>;
+constexpr int kF2MaxThreadsL = LP >= 8 ? 384 : kF2MaxThreads<T, IP>;
 
 // KR: the Kerr (chi(3)) terms are part of the nonlinear step (a separate
 // instantiation, so that the chi(2)-only kernel keeps its registers and code)
@@ -85,7 +92,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
 {
     using V = cv<T>;
     constexpr int Q = 1 << LQ, LN = LP + LQ, N = 1 << LN;
-    constexpr int A2 = (LP + 1) / 2, A1 = LP - A2; // columns [Ra1, Ra2]
+    constexpr int A2 = f2_col_a2(LP), A1 = LP - A2; // columns [Ra1, Ra2]
     constexpr int B2 = (LQ + 1) / 2, B1 = LQ - B2; // rows    [Rb1, Rb2]
     constexpr int Ra1 = 1 << A1, Ra2 = 1 << A2, Rb1 = 1 << B1, Rb2 = 1 << B2;
     constexpr int LS = (LN + 1) / 2; // W_N^a = hi[a >> LS] lo[a & (2^LS - 1)]
