@@ -41,6 +41,7 @@ UNIT = "field-steps/s"
 PEAK_SM_MHZ = 2070.0          # GB300 maximum SM clock
 SMS = 152
 FP32_LANES = 128              # FP32 FMA lanes per SM
+FP64_NOMINAL_TFLOPS = 1.25    # GB300 FP64 (non-tensor), nominal
 
 
 def parse():
@@ -60,6 +61,11 @@ def parse():
     return ap.parse_args()
 
 
+def total_nz(cfg):
+    """z-steps of one round trip: every crystal's."""
+    return cfg.nz + sum(c.nz for c in getattr(cfg, "extra_crystals", ()))
+
+
 def flops_per_roundtrip(cfg):
     """Algorithmic FLOPs of one round trip of one instance (the design doc's model).
 
@@ -70,7 +76,7 @@ def flops_per_roundtrip(cfg):
     point-field: cavity FFT pair 10 log2 N plus 6 (spectral factor) plus 6
     (mirror).
     """
-    n, F, nz = cfg.n, cfg.nfields, cfg.nz
+    n, F, nz = cfg.n, cfg.nfields, total_nz(cfg)
     lg = math.log2(n)
     if F == 3:
         rk4 = 58.0 + (24.0 if cfg.dk != 0 else 0.0)
@@ -404,8 +410,9 @@ def rows_leg(opo, W, prec, local, torch, base, cluster, threads, rounds=2):
     """The widened entry and nonlinear-step variants on the 2^14 workload, in
     the headline's launch shape: ns-pulsed pump (the Gaussian slice evaluated
     at every entry), pump-resonant cavity (input added to the circulating
-    pump), Kerr terms with fourth-order dispersion, and the chi(2)-only
-    workload timed the same way for comparison.  Batch throughput (best of
+    pump), Kerr terms with fourth-order dispersion, the same steps in two
+    crystals, the FP64 path, and the chi(2)-only workload timed the same way
+    for comparison.  Batch throughput (best of
     three runs of ``rounds`` round trips, L2 not flushed) and the fraction of
     the FP32 peak by each variant's own FLOP count."""
     variants = {
@@ -415,18 +422,29 @@ def rows_leg(opo, W, prec, local, torch, base, cluster, threads, rounds=2):
         "pump_resonant_tro": base.replace(resonant_mask=0b111, R=(0.9, 0.98, 0.98),
                                           pump_power=0.05 * base.pump_power),
         "kerr_beta4": base.replace(n2=2e-19, beta4=(4e-55, -3e-55, 2e-55)),
+        # the same 100 steps in two crystals (the second with another phase
+        # mismatch, d_eff and indices)
+        "two_crystals": base.replace(length=base.length / 2, nz=base.nz // 2, extra_crystals=(
+            W.Crystal(length=base.length / 2, nz=base.nz - base.nz // 2, dk=50.0,
+                      deff=0.9 * base.deff, nidx=tuple(1.01 * x for x in base.nidx),
+                      dbeta1=base.dbeta1, beta2=base.beta2, beta3=base.beta3),)),
     }
     peak = SMS * FP32_LANES * 2 * PEAK_SM_MHZ * 1e6 / 1e12
     out = {}
-    for name, cfg in variants.items():
+    # the FP64 path on the same workload, in its own default launch shape
+    # (its fields need twice the shared memory); its fraction is still
+    # quoted against the FP32 peak
+    runs = [(name, cfg, prec, cluster, threads) for name, cfg in variants.items()]
+    runs.append(("chi2_only_fp64", base, opo.OPO_FP64, 0, 0))
+    for name, cfg, pr, cl_req, th_req in runs:
         s = torch.cuda.Stream()
-        probe = opo.Context(cfg, precision=prec, device=local, stream=s.cuda_stream)
+        probe = opo.Context(cfg, precision=pr, device=local, stream=s.cuda_stream)
         ctxs = [probe]
         try:
-            active, cl = opo.opo_fused_capacity(probe.h, cluster, threads)
-            ctxs += [opo.Context(cfg.replace(instance=i), precision=prec, device=local,
+            active, cl = opo.opo_fused_capacity(probe.h, cl_req, th_req)
+            ctxs += [opo.Context(cfg.replace(instance=i), precision=pr, device=local,
                                  stream=s.cuda_stream) for i in range(1, active)]
-            b = opo.opo_batch_create([c.h for c in ctxs], cl, threads)
+            b = opo.opo_batch_create([c.h for c in ctxs], cl, th_req)
             sec = 1e30
             with torch.cuda.stream(s):
                 opo.opo_batch_run(b, 1)
@@ -439,10 +457,13 @@ def rows_leg(opo, W, prec, local, torch, base, cluster, threads, rounds=2):
                     e1.synchronize()
                     sec = min(sec, e0.elapsed_time(e1) * 1e-3)
             opo.opo_batch_destroy(b)
-            fs = active * cfg.nfields * cfg.nz * rounds / sec
+            fs = active * cfg.nfields * total_nz(cfg) * rounds / sec
             tflops = flops_per_roundtrip(cfg) * active * rounds / sec / 1e12
             out[name] = {"instances": active, "cluster": cl, "field_steps_per_s": fs,
                          "tflops": tflops, "frac_fp32_peak": tflops / peak}
+            if pr == opo.OPO_FP64:
+                out[name]["frac_fp64_peak"] = tflops / FP64_NOMINAL_TFLOPS
+                out[name]["fp64_peak_note"] = "nominal GB300 FP64 rate, not measured"
         except opo.OPOError as e:
             out[name] = {"error": str(e)}
         finally:
