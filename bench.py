@@ -499,38 +499,45 @@ def sweep_leg(opo, W, prec, local, torch, rounds=2):
             c.close()
 
 
-def serving_leg(prec, local, batch_value, base, seconds=12.0):
-    """Request stream through the continuous-batching server.  First a
-    saturation run (all requests present at t = 0) measures the server's
-    capacity on this mix; then a Poisson stream at 0.7 of that capacity gives
-    p50/p99 latency.  Round-trip budgets are 50..300 so the runs take seconds."""
+def serving_leg(prec, local, batch_value, base, count=1000):
+    """Request stream through the continuous-batching server: N = 2^12..2^17
+    (2^12..2^16 on the fused path, 2^17 on the plain path), 2 or 3 fields, CW
+    or pulsed.  First a saturation run (all requests present at t = 0)
+    measures the server's capacity on this mix; then ``count`` Poisson
+    arrivals at 0.7 of that capacity give p50/p99 latency.  Round-trip
+    budgets are 20..120 so that the run takes seconds."""
     from paper_2410_02532_gb300 import serving
-    sat = serving.poisson_trace(160, 1e6, seed=20241009, rounds=(50, 300))
+    exps = (12, 13, 14, 15, 16, 17)
+    rounds = (20, 120)
+    sat = serving.poisson_trace(160, 1e6, seed=20241009, n_exps=exps, rounds=rounds)
     srv = serving.Server(precision=prec, device=local, tick_rt=16)
     t0 = time.perf_counter()
     res = srv.run(sat)
     sat_wall = time.perf_counter() - t0
     cap = sum(serving.request_work(r) for r in sat) / sat_wall   # point-field-steps/s
-    probe = serving.poisson_trace(400, 1.0, rounds=(50, 300))
+    probe = serving.poisson_trace(400, 1.0, n_exps=exps, rounds=rounds)
     mean_work = sum(serving.request_work(r) for r in probe) / len(probe)
     rate = 0.7 * cap / mean_work
-    count = max(20, int(rate * seconds))
-    reqs = serving.poisson_trace(count, rate, rounds=(50, 300))
+    reqs = serving.poisson_trace(count, rate, n_exps=exps, rounds=rounds)
     srv = serving.Server(precision=prec, device=local, tick_rt=16)
     t0 = time.perf_counter()
-    res = srv.run(reqs, max_wall_s=4 * seconds)
+    res = srv.run(reqs, max_wall_s=4 * count / rate)
     wall = time.perf_counter() - t0
     st = serving.latency_stats(res)
     done = {x.rid for x in res}
     work = sum(serving.request_work(r) for r in reqs if r.rid in done)
+    # the stream of the full request mix (200 arrivals/s, 100..5000 round trips)
+    full = serving.poisson_trace(400, 1.0, n_exps=exps, rounds=(100, 5000))
+    full_load = 200.0 * sum(serving.request_work(r) for r in full) / len(full) / cap
     st.update({"requests": count, "completed": len(res), "rate_hz": rate,
                "offered_load": 0.7, "capacity_point_field_steps_per_s": cap,
-               "rounds_range": [50, 300], "n_range": [4096, 32768], "wall_s": wall,
-               "point_field_steps_per_s": work / wall, "field_steps_per_s": srv.field_steps / wall,
-               "ticks": srv.ticks, "allocations": srv.allocations,
+               "rounds_range": list(rounds), "n_range": [1 << exps[0], 1 << exps[-1]],
+               "wall_s": wall, "point_field_steps_per_s": work / wall,
+               "field_steps_per_s": srv.field_steps / wall, "ticks": srv.ticks,
+               "allocations": srv.allocations,
                "note": "rate = 0.7 x the server's saturated throughput on the same request mix; "
                        "200 requests/s with 100-5000 round trips would offer about %.0fx that "
-                       "capacity" % (200.0 * (2550.0 / 175.0) * 0.7 / rate)})
+                       "capacity" % full_load})
     return st
 
 
