@@ -369,3 +369,42 @@ def test_output_history_off_and_errors():
         assert ei.value.status == opo.OPO_E_INVALID
         ctx.set_history(0)
         ctx.run(5)  # no limit once off
+
+
+# ------------------------------------- the ns-pulse example of Sec. 4.2
+
+def _rise_and_depletion(cfg, tr):
+    m = np.arange(cfg.M)
+    t = m * cfg.t_rt - cfg.pump_t0
+    p_in = cfg.pump_power * np.exp(-4 * np.log(2) * t ** 2 / cfg.pump_fwhm ** 2)
+    ps, pp = tr[:, 1], tr[:, 0]
+    rise = int(np.argmax(ps > 0.1 * ps.max()))
+    on = p_in > 0.1 * cfg.pump_power
+    return rise, 1.0 - float(np.min(pp[on] / p_in[on]))
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "fused"])
+def test_ns_example_trends(path):
+    """10 ns Gaussian pump of 75, 100 and 250 W peak through the whole pulse
+    (600 round trips from 1e-15 V/m noise): the stronger the pump, the earlier
+    the signal rises and the deeper the pump depletion (the paper's reading
+    of its ns figure); rise round trip within 2 and peak depletion within
+    0.01 of the oracle's."""
+    got = []
+    for peak in (75.0, 100.0, 250.0):
+        cfg = W.ns_pulsed_degenerate(peak_w=peak, n=256)
+        p = orc.params(cfg)
+        _, tr_ref, _, st = orc.run(p, cfg.initial_fields(), None, 0, cfg.M)
+        assert st == 0
+        with opo.Context(cfg, precision=opo.OPO_FP32_PH64) as ctx:
+            ctx.set_path(path)
+            ctx.run(cfg.M)
+            tr = ctx.trace(cfg.M)
+        rise, depl = _rise_and_depletion(cfg, tr)
+        rise_ref, depl_ref = _rise_and_depletion(cfg, tr_ref)
+        assert abs(rise - rise_ref) <= 2, (peak, rise, rise_ref)
+        assert abs(depl - depl_ref) <= 0.01, (peak, depl, depl_ref)
+        got.append((rise, depl))
+    assert got[0][0] > got[1][0] > got[2][0]
+    assert got[0][1] < got[1][1] < got[2][1]
+    assert got[2][1] > 0.3
