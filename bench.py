@@ -368,14 +368,15 @@ def single_and_plain(args, opo, W, base, prec, local, torch, cl_req=0, th_req=0)
 
 
 def e2e(args, opo, W, ctxs, batch, base, torch, np):
-    """Through the C ABI with host buffers: every step copies each instance's
-    fields from pinned host memory, runs one round trip and reads the output
-    signal field and the trace row back to the host."""
+    """Through the C ABI with host buffers: every step copies all instances'
+    fields from pinned host memory (one batch copy), runs one round trip and
+    reads every instance's output signal field and trace row back to the host
+    (one batch copy each)."""
     n, F = base.n, base.nfields
     B = len(ctxs)
-    host_in = [torch.empty((F, n, 2), dtype=torch.float64).pin_memory() for _ in range(B)]
-    host_out = torch.empty((n, 2), dtype=torch.float64).pin_memory()
-    host_tr = torch.empty((1, 4), dtype=torch.float64).pin_memory()
+    host_in = torch.empty((B, F, n, 2), dtype=torch.float64).pin_memory()
+    host_out = torch.empty((B, n, 2), dtype=torch.float64).pin_memory()
+    host_tr = torch.empty((B, 1, 4), dtype=torch.float64).pin_memory()
     for i, c in enumerate(ctxs):
         host_in[i].copy_(torch.from_numpy(np.stack([c.get_fields()[x].view(np.float64).reshape(n, 2)
                                                      for x in range(F)])))
@@ -384,14 +385,10 @@ def e2e(args, opo, W, ctxs, batch, base, torch, np):
     steps = max(3, min(args.steps, 10))
 
     def one_step():
-        for i, c in enumerate(ctxs):
-            for x in range(F):
-                st = L.opo_set_fields(c.h, x, dp(host_in[i][x]), n, -1)
-                assert st == 0
+        assert L.opo_batch_set_fields(batch, dp(host_in), B * F * n) == 0
         opo.opo_batch_run(batch, 1)
-        for c in ctxs:
-            assert L.opo_get_fields(c.h, 1, opo.OPO_OUTPUT, dp(host_out), n) == 0
-            assert L.opo_get_trace(c.h, dp(host_tr), 1) == 0
+        assert L.opo_batch_get_fields(batch, 1, opo.OPO_OUTPUT, dp(host_out), B * n) == 0
+        assert L.opo_batch_get_trace(batch, dp(host_tr), 1) == 0
 
     one_step()
     torch.cuda.synchronize()

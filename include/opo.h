@@ -285,6 +285,23 @@ OPO_API int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t coun
 OPO_API int opo_batch_run(opo_batch *batch, int64_t m);
 OPO_API int opo_batch_destroy(opo_batch *batch);
 
+/* Host transfers of a whole batch (one copy each way instead of one per field
+ * and instance).  opo_batch_set_fields: `host` holds every member's F x N
+ * complex start state, members in batch order, fields in order, interleaved
+ * re/im doubles; count = sum over members of F N (OPO_E_INVALID otherwise).
+ * The round-trip counters are not touched; the host buffer is free to reuse
+ * when the call returns.  opo_batch_get_fields: field `field` (INTRACAVITY or
+ * OUTPUT, as opo_get_fields) of every member into host, members in order, N
+ * complex each (zeros for a member without that field); count = sum of N.
+ * opo_batch_get_trace: the first `rows` trace rows of the last call of every
+ * member, members in order, rows x 4 doubles each (rows at most the last
+ * call's round trips).  Both getters synchronize and return OPO_E_NONFINITE
+ * if any member holds a non-finite field. */
+OPO_API int opo_batch_set_fields(opo_batch *batch, const double *host, size_t count);
+OPO_API int opo_batch_get_fields(opo_batch *batch, int32_t field, int32_t which, double *host,
+                                 size_t count);
+OPO_API int opo_batch_get_trace(opo_batch *batch, double *host, int64_t rows);
+
 /* One crystal pass without any device allocation, for callers that cannot
  * call cudaMalloc (code that runs inside another framework's memory pool or
  * under an allocator that is locked down or already exhausted).  The paper

@@ -60,6 +60,80 @@ __global__ void k_from_f64(cv<T> *dst, const double *src, int n)
         dst[i] = cmk<cv<T>>((T)src[2 * i], (T)src[2 * i + 1]);
 }
 
+// One member of a batch host transfer.
+struct XMember {
+    void *fields, *out;   // F*N state and output fields (context precision)
+    const double *trace;  // rows {P_p, P_s, P_i, nu_c}
+    long long off_all;    // first complex of this member in a [F][N] transfer
+    long long off_n;      // first complex of this member in a one-field transfer
+    int n, F, dbl;
+};
+
+__device__ __forceinline__ int xmember_of(const XMember *m, int count, long long e, bool all)
+{
+    int lo = 0, hi = count - 1; // last member whose offset is <= e
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((all ? m[mid].off_all : m[mid].off_n) <= e)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_batch_from_f64(const XMember *m, int count, const double *src, long long total)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const XMember &x = m[xmember_of(m, count, e, true)];
+        const long long i = e - x.off_all;
+        if (x.dbl)
+            ((double2 *)x.fields)[i] = make_double2(src[2 * e], src[2 * e + 1]);
+        else
+            ((float2 *)x.fields)[i] = make_float2((float)src[2 * e], (float)src[2 * e + 1]);
+    }
+}
+
+__global__ void k_batch_to_f64(const XMember *m, int count, int field, int which, double *dst,
+                               long long total)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const XMember &x = m[xmember_of(m, count, e, false)];
+        const long long i = (long long)field * x.n + (e - x.off_n);
+        double re = 0.0, im = 0.0;
+        if (field < x.F) {
+            const void *b = which == OPO_OUTPUT ? x.out : x.fields;
+            if (x.dbl) {
+                const double2 v = ((const double2 *)b)[i];
+                re = v.x;
+                im = v.y;
+            } else {
+                const float2 v = ((const float2 *)b)[i];
+                re = (double)v.x;
+                im = (double)v.y;
+            }
+        }
+        dst[2 * e] = re;
+        dst[2 * e + 1] = im;
+    }
+}
+
+__global__ void k_batch_trace(const XMember *m, int count, int rows, double *dst)
+{
+    const long long per = 4LL * rows, total = per * count;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        dst[e] = m[e / per].trace[e % per];
+}
+
+__global__ void k_gather_err(int *const *src, int count, int *dst)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        dst[i] = *src[i];
+}
+
 template <class T>
 __global__ void k_to_f64(double *dst, const cv<T> *src, int n)
 {
@@ -795,10 +869,20 @@ struct opo_batch {
     cudaEvent_t fork = nullptr;
     int device = 0;              // copies, so that destroying the batch never
     cudaStream_t stream = nullptr; // reads a member context
+    // host transfers of the whole batch (allocated on first use)
+    double *d_xfer = nullptr;    // staging, FP64 interleaved
+    size_t xfer_cap = 0;         // doubles
+    XMember *d_mem = nullptr;    // member table of the transfer kernels
+    std::vector<XMember> h_mem;
+    int **d_err = nullptr;       // members' sticky error words
+    int *d_errs = nullptr;       // their copies, one per member
 };
 
 static void batch_free(opo_batch *b)
 {
+    for (void *p : {(void *)b->d_xfer, (void *)b->d_err, (void *)b->d_errs, (void *)b->d_mem})
+        if (p)
+            cudaFree(p);
     for (BatchGroup &g : b->groups) {
         if (g.stream)
             cudaStreamDestroy(g.stream);
@@ -899,6 +983,204 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
     }
     *out = b;
     return OPO_OK;
+}
+
+namespace {
+
+// Order the batch's stream after every member's stream (in) or every
+// member's stream after the batch's (out).
+void batch_fence(opo_batch *b, cudaStream_t s, bool in)
+{
+    for (size_t i = 0; i < b->ctxs.size(); i++) {
+        opo_ctx *c = b->ctxs[i];
+        if (c->stream == s)
+            continue;
+        cudaEventRecord(b->ev[i], in ? c->stream : s);
+        cudaStreamWaitEvent(in ? s : c->stream, b->ev[i], 0);
+    }
+}
+
+int batch_staging(opo_batch *b, size_t doubles)
+{
+    if (doubles <= b->xfer_cap)
+        return OPO_OK;
+    cudaStreamSynchronize(b->stream);
+    if (b->d_xfer)
+        cudaFree(b->d_xfer);
+    b->d_xfer = nullptr;
+    b->xfer_cap = 0;
+    if (cudaMalloc((void **)&b->d_xfer, sizeof(double) * doubles) != cudaSuccess) {
+        cudaGetLastError();
+        return OPO_E_NOMEM;
+    }
+    b->xfer_cap = doubles;
+    return OPO_OK;
+}
+
+// Upload the member table (pointers can change: the trace grows with M).
+int batch_members(opo_batch *b, cudaStream_t s)
+{
+    const int count = (int)b->ctxs.size();
+    if (!b->d_mem && cudaMalloc((void **)&b->d_mem, sizeof(XMember) * count) != cudaSuccess) {
+        b->d_mem = nullptr;
+        cudaGetLastError();
+        return OPO_E_NOMEM;
+    }
+    b->h_mem.resize(count);
+    long long oa = 0, on = 0;
+    for (int i = 0; i < count; i++) {
+        const opo_ctx *c = b->ctxs[i];
+        XMember &x = b->h_mem[i];
+        x.fields = c->d_fields;
+        x.out = c->d_out;
+        x.trace = c->d_trace;
+        x.off_all = oa;
+        x.off_n = on;
+        x.n = c->n;
+        x.F = c->F;
+        x.dbl = c->prec == OPO_FP64;
+        oa += (long long)c->F * c->n;
+        on += c->n;
+    }
+    // the pageable source is staged before cudaMemcpyAsync returns
+    return cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(XMember) * count,
+                           cudaMemcpyHostToDevice, s) == cudaSuccess
+               ? OPO_OK
+               : OPO_E_CUDA;
+}
+
+int xblocks(long long work)
+{
+    long long g = (work + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(g, 4096));
+}
+
+// Wait for the batch's stream, then OPO_E_NONFINITE if any member has set
+// its error word (one gather, one copy).
+int batch_check_err(opo_batch *b)
+{
+    const int count = (int)b->ctxs.size();
+    if (!b->d_err) {
+        std::vector<int *> p(count);
+        for (int i = 0; i < count; i++)
+            p[i] = (int *)((char *)b->ctxs[i]->d_ctl + offsetof(DevCtl, err));
+        if (cudaMalloc((void **)&b->d_err, sizeof(int *) * count) != cudaSuccess ||
+            cudaMalloc((void **)&b->d_errs, sizeof(int) * count) != cudaSuccess) {
+            cudaGetLastError();
+            return OPO_E_NOMEM;
+        }
+        if (cudaMemcpy(b->d_err, p.data(), sizeof(int *) * count, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+            return OPO_E_CUDA;
+    }
+    k_gather_err<<<1, 256, 0, b->stream>>>(b->d_err, count, b->d_errs);
+    std::vector<int> e(count);
+    if (cudaMemcpyAsync(e.data(), b->d_errs, sizeof(int) * count, cudaMemcpyDeviceToHost,
+                        b->stream) != cudaSuccess)
+        return OPO_E_CUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return OPO_E_CUDA;
+    for (int v : e)
+        if (v)
+            return OPO_E_NONFINITE;
+    return OPO_OK;
+}
+
+} // namespace
+
+int opo_batch_set_fields(opo_batch *b, const double *host, size_t count)
+{
+    if (!b || !host)
+        return OPO_E_INVALID;
+    size_t total = 0;
+    for (const opo_ctx *c : b->ctxs)
+        total += (size_t)c->F * c->n;
+    if (count != total)
+        return OPO_E_INVALID;
+    DeviceGuard g(b->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    int rc = batch_staging(b, 2 * total);
+    if (rc != OPO_OK)
+        return rc;
+    cudaStream_t s = b->stream;
+    batch_fence(b, s, true);
+    rc = batch_members(b, s);
+    if (rc != OPO_OK)
+        return rc;
+    if (cudaMemcpyAsync(b->d_xfer, host, sizeof(double) * 2 * total, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return OPO_E_CUDA;
+    k_batch_from_f64<<<xblocks((long long)total), 256, 0, s>>>(b->d_mem, (int)b->ctxs.size(),
+                                                               b->d_xfer, (long long)total);
+    if (cudaGetLastError() != cudaSuccess)
+        return OPO_E_CUDA;
+    batch_fence(b, s, false);
+    // the host buffer is free to reuse when this returns
+    return cudaStreamSynchronize(s) == cudaSuccess ? OPO_OK : OPO_E_CUDA;
+}
+
+int opo_batch_get_fields(opo_batch *b, int32_t field, int32_t which, double *host, size_t count)
+{
+    if (!b || !host || field < 0 || field > 2 || (which != OPO_INTRACAVITY && which != OPO_OUTPUT))
+        return OPO_E_INVALID;
+    size_t total = 0;
+    for (const opo_ctx *c : b->ctxs)
+        total += (size_t)c->n;
+    if (count != total)
+        return OPO_E_INVALID;
+    DeviceGuard g(b->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    int rc = batch_staging(b, 2 * total);
+    if (rc != OPO_OK)
+        return rc;
+    cudaStream_t s = b->stream;
+    batch_fence(b, s, true);
+    rc = batch_members(b, s);
+    if (rc != OPO_OK)
+        return rc;
+    k_batch_to_f64<<<xblocks((long long)total), 256, 0, s>>>(b->d_mem, (int)b->ctxs.size(), field,
+                                                             which, b->d_xfer, (long long)total);
+    if (cudaGetLastError() != cudaSuccess)
+        return OPO_E_CUDA;
+    if (cudaMemcpyAsync(host, b->d_xfer, sizeof(double) * 2 * total, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return OPO_E_CUDA;
+    batch_fence(b, s, false);
+    return batch_check_err(b);
+}
+
+int opo_batch_get_trace(opo_batch *b, double *host, int64_t rows)
+{
+    if (!b || !host || rows < 0)
+        return OPO_E_INVALID;
+    for (const opo_ctx *c : b->ctxs)
+        if (rows > c->last_M)
+            return OPO_E_INVALID;
+    DeviceGuard g(b->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    const size_t per = 4 * (size_t)rows;
+    int rc = batch_staging(b, per * b->ctxs.size());
+    if (rc != OPO_OK)
+        return rc;
+    cudaStream_t s = b->stream;
+    batch_fence(b, s, true);
+    rc = batch_members(b, s);
+    if (rc != OPO_OK)
+        return rc;
+    if (rows > 0) {
+        k_batch_trace<<<xblocks((long long)per * (long long)b->ctxs.size()), 256, 0, s>>>(
+            b->d_mem, (int)b->ctxs.size(), (int)rows, b->d_xfer);
+        if (cudaGetLastError() != cudaSuccess)
+            return OPO_E_CUDA;
+    }
+    if (rows > 0 && cudaMemcpyAsync(host, b->d_xfer, sizeof(double) * per * b->ctxs.size(),
+                                    cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return OPO_E_CUDA;
+    batch_fence(b, s, false);
+    return batch_check_err(b);
 }
 
 int opo_batch_run(opo_batch *b, int64_t m)

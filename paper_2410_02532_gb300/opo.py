@@ -95,6 +95,10 @@ _SIGS = {
                           ctypes.c_int32], ctypes.c_int),
     "opo_batch_run": ([_P, ctypes.c_int64], ctypes.c_int),
     "opo_batch_destroy": ([_P], ctypes.c_int),
+    "opo_batch_set_fields": ([_P, _DP, ctypes.c_size_t], ctypes.c_int),
+    "opo_batch_get_fields": ([_P, ctypes.c_int32, ctypes.c_int32, _DP, ctypes.c_size_t],
+                             ctypes.c_int),
+    "opo_batch_get_trace": ([_P, _DP, ctypes.c_int64], ctypes.c_int),
 }
 
 
@@ -238,6 +242,29 @@ def opo_batch_run(batch, m: int):
 
 def opo_batch_destroy(batch):
     lib().opo_batch_destroy(batch)
+
+
+def opo_batch_set_fields(batch, host):
+    """host: complex128 array holding every member's F x N fields in batch
+    order (a flat array of sum F N values, or anything that flattens to it;
+    a pinned contiguous buffer avoids a staging copy in the driver)."""
+    a = np.ascontiguousarray(host, dtype=np.complex128).reshape(-1)
+    _check(lib().opo_batch_set_fields(batch, a.ctypes.data_as(_DP), a.size),
+           "opo_batch_set_fields")
+
+
+def opo_batch_get_fields(batch, field, which, total_n):
+    out = np.empty(int(total_n), dtype=np.complex128)
+    _check(lib().opo_batch_get_fields(batch, int(field), int(which), out.ctypes.data_as(_DP),
+                                      out.size), "opo_batch_get_fields")
+    return out
+
+
+def opo_batch_get_trace(batch, count, rows):
+    out = np.empty((int(count), int(rows), 4), dtype=np.float64)
+    _check(lib().opo_batch_get_trace(batch, out.ctypes.data_as(_DP), int(rows)),
+           "opo_batch_get_trace")
+    return out
 
 
 # ---- structs from a workload configuration ---------------------------------

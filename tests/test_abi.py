@@ -69,6 +69,11 @@ def test_null_arguments(L):
     assert L.opo_run_roundtrips(None, 1, None) == opo.OPO_E_INVALID
     assert L.opo_destroy(None) == opo.OPO_OK
     assert L.opo_batch_create(None, None, 0, 0, 0) == opo.OPO_E_INVALID
+    assert L.opo_batch_set_fields(None, None, 0) == opo.OPO_E_INVALID
+    assert L.opo_batch_get_fields(None, 0, 0, None, 0) == opo.OPO_E_INVALID
+    assert L.opo_batch_get_trace(None, None, 0) == opo.OPO_E_INVALID
+    assert L.opo_set_output_history(None, 1) == opo.OPO_E_INVALID
+    assert L.opo_get_output_history(None, 0, 0, 1, None) == opo.OPO_E_INVALID
 
 
 def _have_gpu():

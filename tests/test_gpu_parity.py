@@ -458,3 +458,50 @@ def test_fused_n65536_batch_resume_bitwise():
     finally:
         for c in ctxs:
             c.close()
+
+
+# ---------------------------------------- host transfers of a whole batch
+
+def test_batch_host_transfers_match_per_context_calls():
+    """One copy in and one copy out for the whole batch (mixed sizes, field
+    counts and precisions of the fields stay per member) equal the per-context
+    calls bit for bit."""
+    cfgs = [cfg_dispersive(n=1024, nz=3), cfg_degenerate(n=2048).replace(nz=3),
+            cfg_dispersive(n=16384, nz=2), cfg_dro(n=4096).replace(nz=2)]
+    starts = [strong(c, 2e6, i) for i, c in enumerate(cfgs)]
+    # reference: per-context transfers
+    ref_f, ref_t, ref_s = [], [], []
+    for c, a in zip(cfgs, starts):
+        with opo.Context(c) as ctx:
+            ctx.set_fields(a)
+            ctx.set_path(opo.OPO_PATH_FUSED)
+            ctx.run(2)
+            ref_f.append(ctx.get_fields(opo.OPO_OUTPUT))
+            ref_s.append(ctx.get_fields())
+            ref_t.append(ctx.trace(2))
+    ctxs = [opo.Context(c) for c in cfgs]
+    try:
+        b = opo.opo_batch_create([c.h for c in ctxs], 0, 0)
+        opo.opo_batch_set_fields(b, np.concatenate([a.reshape(-1) for a in starts]))
+        opo.opo_batch_run(b, 2)
+        total = sum(c.n for c in cfgs)
+        for x in range(3):
+            for which, ref in ((opo.OPO_OUTPUT, ref_f), (opo.OPO_INTRACAVITY, ref_s)):
+                got = opo.opo_batch_get_fields(b, x, which, total)
+                off = 0
+                for c, r in zip(cfgs, ref):
+                    seg = got[off:off + c.n]
+                    if x < c.nfields:
+                        assert np.array_equal(seg, r[x])
+                    else:
+                        assert np.all(seg == 0)
+                    off += c.n
+        tr = opo.opo_batch_get_trace(b, len(cfgs), 2)
+        for i in range(len(cfgs)):
+            assert np.array_equal(tr[i], ref_t[i])
+        with pytest.raises(opo.OPOError):
+            opo.opo_batch_set_fields(b, np.zeros(7, complex))  # wrong size
+        opo.opo_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            c.close()
