@@ -18,7 +18,7 @@ import threading
 
 from . import opo
 
-CLUSTERS = (4, 8, 16)
+CLUSTERS = (1, 2, 4, 8, 16)
 THREADS = (0, 128, 192, 256, 384, 512)
 RT_PER_LAUNCH = (16, 64)
 

@@ -25,7 +25,7 @@ int dispatch(int op, bool ip, bool kr, bool dbl, int F, int logn, const InstDesc
 // In-place variant: X and Y only, dispersion factors from L2.
 bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
-    if (logn < 14 || logn > 16 || (logn == 16 && dbl))
+    if (logn < 12 || logn > 16 || (logn == 16 && dbl))
         return false;
     const int LP = logn / 2, LQ = logn - LP;
     if ((1 << LP) < C || (1 << LQ) < C)

@@ -834,8 +834,8 @@ int max_active_t(int C, int threads, size_t sm)
 }
 
 // Launch (op 0) or occupancy query (op 1) of every instantiated size for one
-// precision and field count; ip selects the in-place variant (2^14 and 2^15
-// only), kr the instantiation with the Kerr terms.  The chi(2)-only and the
+// precision and field count; ip selects the in-place variant, kr the
+// instantiation with the Kerr terms.  The chi(2)-only and the
 // Kerr instantiations of a precision and field count are defined in two
 // translation units (opo_fused2_<prec>_<F>.cu and ..._kerr.cu) that compile in
 // parallel.
@@ -863,6 +863,10 @@ OPO_F2_DISPATCH_KR_DECL(dispatch_f64_f2_kerr);
 #define OPO_F2_SIZES(T, F, KR)                                                                   \
     if (ip) {                                                                                    \
         switch (logn) {                                                                          \
+        case 12:                                                                                 \
+            OPO_F2_ONE(T, F, 6, 6, true, KR);                                                    \
+        case 13:                                                                                 \
+            OPO_F2_ONE(T, F, 6, 7, true, KR);                                                    \
         case 14:                                                                                 \
             OPO_F2_ONE(T, F, 7, 7, true, KR);                                                    \
         case 15:                                                                                 \

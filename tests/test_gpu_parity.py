@@ -375,6 +375,12 @@ IP_CASES = [
     ("dro_32768_c8", lambda: cfg_dro(n=32768).replace(nz=2), opo.OPO_FP32_PH64, 8),
     ("deg_16384_c4", lambda: cfg_degenerate(n=16384).replace(nz=3), opo.OPO_FP32_PH64, 4),
     ("sro_16384_fp64_c8", lambda: cfg_dispersive(n=16384, nz=2), opo.OPO_FP64, 8),
+    # one CTA per instance (no cluster exchange) and two-CTA clusters
+    ("sro_4096_c1", lambda: cfg_dispersive(n=4096, nz=4), opo.OPO_FP32_PH64, 1),
+    ("sync_4096_c1", lambda: cfg_sync(n=4096).replace(nz=4), opo.OPO_FP32_PH64, 1),
+    ("deg_8192_c2", lambda: cfg_degenerate(n=8192).replace(nz=4), opo.OPO_FP32_PH64, 2),
+    ("dro_8192_c2", lambda: cfg_dro(n=8192).replace(nz=3), opo.OPO_FP32_PH64, 2),
+    ("sro_4096_fp64_c2", lambda: cfg_dispersive(n=4096, nz=3), opo.OPO_FP64, 2),
 ]
 
 
