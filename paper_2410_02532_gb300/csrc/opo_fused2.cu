@@ -42,7 +42,9 @@ bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, Fused
     (void)A2;
     const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
     const int LS = (logn + 1) / 2;
-    size_t el = (size_t)F * nc * 2 + (1 << LQ) + (1 << LS) + ((1 << logn) >> LS);
+    // X, Y; stage twiddles (2P + 2Q); W_N halves (lo, hi)
+    size_t el = (size_t)F * nc * 2 + 2 * (1 << LP) + 2 * (1 << LQ) + (1 << LS) +
+                ((1 << logn) >> LS);
     size_t sm = el * csz + 32 * kNslot * sizeof(double);
     if (sm > 227 * 1024)
         return false;
@@ -85,7 +87,8 @@ bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_
     (void)B2;
     (void)Pc;
     for (int ds = 1; ds >= 0; ds--) {
-        size_t el = (size_t)F * nc * (ds ? 4 : 3) + (1 << LQ) + (1 << LS) + ((1 << logn) >> LS);
+        size_t el = (size_t)F * nc * (ds ? 4 : 3) + 2 * (1 << LP) + 2 * (1 << LQ) + (1 << LS) +
+                    ((1 << logn) >> LS);
         size_t sm = el * csz + 32 * kNslot * sizeof(double);
         if (sm > 227 * 1024)
             continue;

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     k_fused2(const InstDesc *__restrict__ descs, int r_base, int M, int write_out, int disp_smem)
 {
     using V = cv<T>;
-    constexpr int Q = 1 << LQ, LN = LP + LQ, N = 1 << LN;
+    constexpr int P = 1 << LP, Q = 1 << LQ, LN = LP + LQ, N = 1 << LN;
     constexpr int A2 = f2_col_a2(LP), A1 = LP - A2; // columns [Ra1, Ra2]
     constexpr int B2 = (LQ + 1) / 2, B1 = LQ - B2; // rows    [Rb1, Rb2]
     constexpr int Ra1 = 1 << A1, Ra2 = 1 << A2, Rb1 = 1 << B1, Rb2 = 1 << B2;
@@ -113,8 +113,15 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     V *Y = X + F * NC;
     V *S = IP ? nullptr : Y + F * NC;
     V *Dsm = IP ? Y + F * NC : S + F * NC;
-    V *twQ = Dsm + (disp_smem ? F * NC : 0);
-    V *twLo = twQ + Q;
+    // stage twiddles W^{r j}, indexed [r][j] with j the butterfly index that
+    // runs along consecutive lanes: the loads of one r hit consecutive
+    // words (or one broadcast word) and sit at constant offsets from the
+    // item's base
+    V *twA = Dsm + (disp_smem ? F * NC : 0); // W_P, r < Ra1, j < Ra2 (block A)
+    V *tw2 = twA + P;                         // W_P, r < Ra2, j < Ra1 (phase 2)
+    V *twB = tw2 + P;                         // W_Q, r < Rb2, j < Rb1 (block B)
+    V *tw5 = twB + Q;                         // W_Q, r < Rb1, j < Rb2 (phase 5)
+    V *twLo = tw5 + Q;
     V *twHi = twLo + (1 << LS);
     double *red = reinterpret_cast<double *>(twHi + (N >> LS));
     __shared__ V *rX[kMaxCl];
@@ -167,8 +174,15 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     double *obs = dg.obs;
     int *err = dg.err;
 
-    for (int i = threadIdx.x; i < Q; i += blockDim.x)
-        twQ[i] = gtw[i << LP];
+    // W_P^e = gtw[e << LQ], W_Q^e = gtw[e << LP]
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        twA[i] = gtw[((i >> A2) * (i & (Ra2 - 1))) << LQ];
+        tw2[i] = gtw[((i >> A1) * (i & (Ra1 - 1))) << LQ];
+    }
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+        twB[i] = gtw[((i >> B1) * (i & (Rb1 - 1))) << LP];
+        tw5[i] = gtw[((i >> B2) * (i & (Rb2 - 1))) << LP];
+    }
     for (int i = threadIdx.x; i < (1 << LS); i += blockDim.x)
         twLo[i] = gtw[i];
     for (int i = threadIdx.x; i < (N >> LS); i += blockDim.x)
@@ -209,7 +223,6 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     auto CI = [=](int f, int n1, int b) { return IP ? cidx_ip(f, n1, b) : cidx(f, n1, b); };
     auto RI = [=](int f, int row, int e) { return IP ? ridx_ip(f, row, e) : ridx(f, row, e); };
     auto gtime = [=](int n1, int b) { return (n1 << LQ) + (c << logQc) + b; };
-    auto twP = [&](int e) { return twQ[e << (LQ - LP)]; }; // W_P^e
     auto twN = [&](unsigned a) {
         a &= (unsigned)(N - 1);
         return cmul(twHi[a >> LS], twLo[a & ((1u << LS) - 1)]);
@@ -295,7 +308,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 for (int f = 0; f < F; f++) {
 #pragma unroll
                     for (int r = 1; r < Ra1; r++) {
-                        V w = twP(r * j);
+                        V w = twA[r * Ra2 + j];
                         w.y = -w.y;
                         v[f][r] = cmul(v[f][r], w);
                     }
@@ -447,7 +460,9 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
 #pragma unroll 1
             for (int base = 0; base < items; base += blockDim.x) {
                 // lanes past the end redo the last item and drop it, so the
-                // warp stays converged around the barrier
+                // warp stays converged around the barrier (warps wholly past
+                // the end run the round too: letting them skip it measured
+                // 1-8% slower)
                 const int u0 = base + threadIdx.x;
                 const bool have = u0 < items;
                 const int u = have ? u0 : items - 1;
@@ -485,7 +500,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 v[r] = X[CI(f, j + r * Ra1, b)];
 #pragma unroll
             for (int r = 1; r < Ra2; r++)
-                v[r] = cmul(v[r], twP(r * j));
+                v[r] = cmul(v[r], tw2[r * Ra1 + j]);
             dft_r<Ra2, -1>(v);
             const int n2 = (c << logQc) + b;
             // W_N^{n2 k1} for k1 = j + r Ra1: base W_N^{n2 j} times step^r
@@ -581,7 +596,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             }
 #pragma unroll
             for (int r = 1; r < Rb2; r++)
-                v[r] = cmul(v[r], twQ[r * j]);
+                v[r] = cmul(v[r], twB[r * Rb1 + j]);
             dft_r<Rb2, -1>(v);
 #pragma unroll
             for (int r = 0; r < Rb2; r++) {
@@ -658,7 +673,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 v[r] = Y[RI(f, row, j + r * Rb2)];
 #pragma unroll
             for (int r = 1; r < Rb1; r++) {
-                V w = twQ[r * j];
+                V w = tw5[r * Rb2 + j];
                 w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
