@@ -16,7 +16,8 @@ LIB = os.path.join(HERE, "libopo.so")
 SOURCES = ["opo_abi.cu", "opo_setup.cu", "opo_plain.cu", "opo_fused.cu", "opo_fused2.cu",
            "opo_fused2_f32_f3.cu", "opo_fused2_f32_f2.cu", "opo_fused2_f64_f3.cu",
            "opo_fused2_f64_f2.cu", "opo_fused2_f32_f3_kerr.cu", "opo_fused2_f32_f2_kerr.cu",
-           "opo_fused2_f64_f3_kerr.cu", "opo_fused2_f64_f2_kerr.cu", "opo_noalloc.cu"]
+           "opo_fused2_f64_f3_kerr.cu", "opo_fused2_f64_f2_kerr.cu", "opo_fused2_f32_f3_nodk.cu",
+           "opo_fused2_f32_f2_nodk.cu", "opo_noalloc.cu"]
 HEADERS = ["opo_common.cuh", "opo_internal.h", "opo_fused_desc.cuh", "opo_fused2.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -210,6 +210,7 @@ int derive(opo_ctx *c)
     // setup); the specialised kernels take the Kerr instantiation when any
     // crystal has the terms
     c->kerr_any = false;
+    c->dk_any = false;
     for (int i = 0; i < c->ncry; i++) {
         const opo_crystal &ki = c->cry[i];
         CryDesc &cd = c->h_cry[i];
@@ -220,6 +221,7 @@ int derive(opo_ctx *c)
         cd.use_dk = ki.dk_per_m != 0.0;
         cd.kerr = kerr_coefficients(ki, c->F, cd.kerr_g);
         c->kerr_any = c->kerr_any || cd.kerr;
+        c->dk_any = c->dk_any || cd.use_dk;
     }
     d.ns = NsPump{};
     d.ns.n = c->n;
@@ -357,7 +359,7 @@ int choose_path(opo_ctx *c, FusedCfg *cfg)
     if (c->path_req == OPO_PATH_PLAIN)
         return OPO_PATH_PLAIN;
     bool ok = fused_config(c->csz, c->F, c->F, c->n, c->n, c->cluster_req, c->rtpl_req,
-                           c->threads_req, c->kerr_any, cfg);
+                           c->threads_req, nl_variant(c), cfg);
     if (c->path_req == OPO_PATH_FUSED)
         return ok ? OPO_PATH_FUSED : -1;
     return ok ? OPO_PATH_FUSED : OPO_PATH_PLAIN;
@@ -681,7 +683,7 @@ int opo_set_path(opo_ctx *c, int32_t path, int32_t cluster, int32_t rt_per_launc
         FusedCfg cfg;
         DeviceGuard g(c->device);
         if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, rt_per_launch, threads,
-                          c->kerr_any, &cfg))
+                          nl_variant(c), &cfg))
             return OPO_E_UNSUPPORTED;
     }
     c->path_req = path;
@@ -833,7 +835,7 @@ int opo_fused_capacity(const opo_ctx *c, int32_t cluster, int32_t threads, int32
     if (!g.ok)
         return OPO_E_CUDA;
     FusedCfg cfg;
-    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, threads, c->kerr_any, &cfg))
+    if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cluster, 0, threads, nl_variant(c), &cfg))
         return OPO_E_UNSUPPORTED;
     *max_active = fused_max_active(c->prec == OPO_FP64, c->F, c->n, cfg);
     if (cluster_out)
@@ -947,14 +949,14 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
             const opo_ctx *g0 = b->groups[k].ctxs[0];
             int cl0, th0, rt0;
             want(g0, &cl0, &th0, &rt0);
-            if (g0->n == c->n && g0->F == c->F && g0->kerr_any == c->kerr_any && cl0 == cl &&
+            if (g0->n == c->n && g0->F == c->F && nl_variant(g0) == nl_variant(c) && cl0 == cl &&
                 th0 == th && rt0 == rt)
                 gi = (int)k;
         }
         if (gi < 0) {
             b->groups.emplace_back();
             gi = (int)b->groups.size() - 1;
-            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, c->kerr_any,
+            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, nl_variant(c),
                               &b->groups[gi].cfg)) {
                 batch_free(b);
                 return OPO_E_UNSUPPORTED;

@@ -36,6 +36,8 @@ template <class V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a
 // of a crystal, one or many instances) round the same.
 __device__ __forceinline__ float fmad_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmad_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fadd_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double fadd_(double a, double b) { return __dadd_rn(a, b); }
 template <class V> __device__ __forceinline__ V cmul(V a, V b)
 {
     return cmk<V>(fmad_(a.x, b.x, -(a.y * b.y)), fmad_(a.x, b.y, a.y * b.x));
@@ -151,15 +153,17 @@ __host__ __device__ inline RadixPlan make_plan(int log2L)
 // One classic RK4 step of size h from z0 uses the products at the stage
 // points (stage factors e0 = e^{i dk z0}, e1 = e^{i dk (z0 + h/2)},
 // e2 = e^{i dk (z0 + h)}); the constants i c_x h/2, i c_x h and i c_x h/6 are
-// folded into the fused multiply-adds of the stage updates.
-template <int F, class V>
+// folded into the fused multiply-adds of the stage updates.  EM: whether the
+// phase factors enter (0: never, dk = 0; 2: where the runtime flag use_e says
+// so, which compiles to predicated products).
+template <int F, int EM, class V>
 __device__ __forceinline__ void nl_prod(const V *a, V e, bool use_e, V *p)
 {
     if constexpr (F == 3) {
         p[0] = cmul(a[1], a[2]);  // A_s A_i
         p[1] = cmulc(a[0], a[2]); // A_p A_i*
         p[2] = cmulc(a[0], a[1]); // A_p A_s*
-        if (use_e) {
+        if (EM == 2 && use_e) {
             p[0] = cmulc(p[0], e);
             p[1] = cmul(p[1], e);
             p[2] = cmul(p[2], e);
@@ -167,24 +171,25 @@ __device__ __forceinline__ void nl_prod(const V *a, V e, bool use_e, V *p)
     } else {
         p[0] = cmul(a[1], a[1]);  // A_s^2
         p[1] = cmulc(a[0], a[1]); // A_p A_s*
-        if (use_e) {
+        if (EM == 2 && use_e) {
             p[0] = cmulc(p[0], e);
             p[1] = cmul(p[1], e);
         }
     }
 }
 
-// y + g (i p) for real g
+// y + g (i p) for real g (explicit multiply-adds: every compiled copy of the
+// RK4 step rounds alike, whatever the surrounding code)
 template <class V>
 __device__ __forceinline__ V add_ig(V y, typename cscal<V>::type g, V p)
 {
     return cmk<V>(y.x - g * p.y, y.y + g * p.x);
 }
 
-template <int F, class V>
-__device__ __forceinline__ void rk4_point(V *y, V e0, V e1, V e2,
-                                          const typename cscal<V>::type *kap,
-                                          typename cscal<V>::type h, bool use_e)
+template <int F, int EM, class V>
+__device__ __forceinline__ void rk4_point_e(V *y, V e0, V e1, V e2,
+                                            const typename cscal<V>::type *kap,
+                                            typename cscal<V>::type h, bool use_e)
 {
     using S = typename cscal<V>::type;
     S c[F], ch[F], c6[F];
@@ -196,19 +201,19 @@ __device__ __forceinline__ void rk4_point(V *y, V e0, V e1, V e2,
         c[x] = c[x] * h;
     }
     V p1[F], p2[F], p3[F], p4[F], t[F];
-    nl_prod<F>(y, e0, use_e, p1);
+    nl_prod<F, EM>(y, e0, use_e, p1);
 #pragma unroll
     for (int x = 0; x < F; x++)
         t[x] = add_ig(y[x], ch[x], p1[x]);
-    nl_prod<F>(t, e1, use_e, p2);
+    nl_prod<F, EM>(t, e1, use_e, p2);
 #pragma unroll
     for (int x = 0; x < F; x++)
         t[x] = add_ig(y[x], ch[x], p2[x]);
-    nl_prod<F>(t, e1, use_e, p3);
+    nl_prod<F, EM>(t, e1, use_e, p3);
 #pragma unroll
     for (int x = 0; x < F; x++)
         t[x] = add_ig(y[x], c[x], p3[x]);
-    nl_prod<F>(t, e2, use_e, p4);
+    nl_prod<F, EM>(t, e2, use_e, p4);
 #pragma unroll
     for (int x = 0; x < F; x++) {
         S sx = p1[x].x + (S)2 * p2[x].x + (S)2 * p3[x].x + p4[x].x;
@@ -221,11 +226,11 @@ __device__ __forceinline__ void rk4_point(V *y, V e0, V e1, V e2,
 //   dA_x/dz = i (c_x p_x + g_x A_x),  g_x = sum_y G_xy |A_y|^2,
 // where G_xy = (2 pi/lambda_x) n2 n_y eps0 c/2 times 1 (y = x) or 2 (y != x)
 // gives self- and cross-phase modulation.  G is row-major 3 x 3.
-template <int F, class V>
-__device__ __forceinline__ void rk4_point_kerr(V *y, V e0, V e1, V e2,
-                                               const typename cscal<V>::type *kap,
-                                               typename cscal<V>::type h, bool use_e,
-                                               const typename cscal<V>::type *G)
+template <int F, int EM, class V>
+__device__ __forceinline__ void rk4_point_kerr_e(V *y, V e0, V e1, V e2,
+                                                 const typename cscal<V>::type *kap,
+                                                 typename cscal<V>::type h, bool use_e,
+                                                 const typename cscal<V>::type *G)
 {
     using S = typename cscal<V>::type;
     S c[F];
@@ -234,7 +239,7 @@ __device__ __forceinline__ void rk4_point_kerr(V *y, V e0, V e1, V e2,
         c[x] = (F == 2 && x == 0) ? kap[0] * (S)0.5 : kap[x];
     auto rhs = [&](const V *a, V e, V *q) {
         V p[F];
-        nl_prod<F>(a, e, use_e, p);
+        nl_prod<F, EM>(a, e, use_e, p);
         S i2[F];
 #pragma unroll
         for (int x = 0; x < F; x++)
@@ -269,6 +274,23 @@ __device__ __forceinline__ void rk4_point_kerr(V *y, V e0, V e1, V e2,
         S sy = q1[x].y + (S)2 * q2[x].y + (S)2 * q3[x].y + q4[x].y;
         y[x] = add_ig(y[x], h6, cmk<V>(sx, sy));
     }
+}
+
+template <int F, class V>
+__device__ __forceinline__ void rk4_point(V *y, V e0, V e1, V e2,
+                                          const typename cscal<V>::type *kap,
+                                          typename cscal<V>::type h, bool use_e)
+{
+    rk4_point_e<F, 2>(y, e0, e1, e2, kap, h, use_e);
+}
+
+template <int F, class V>
+__device__ __forceinline__ void rk4_point_kerr(V *y, V e0, V e1, V e2,
+                                               const typename cscal<V>::type *kap,
+                                               typename cscal<V>::type h, bool use_e,
+                                               const typename cscal<V>::type *G)
+{
+    rk4_point_kerr_e<F, 2>(y, e0, e1, e2, kap, h, use_e, G);
 }
 
 // --------------------------------------------------- shared context ----

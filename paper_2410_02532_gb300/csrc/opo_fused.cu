@@ -427,7 +427,7 @@ bool cluster_launchable(bool dbl, int C, size_t sm)
 } // namespace
 
 bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluster_req,
-                  int rtpl_req, int threads_req, bool kerr, FusedCfg *out)
+                  int rtpl_req, int threads_req, int nl, FusedCfg *out)
 {
     const bool dbl = csz == sizeof(double2);
     const int lognmin = ilog2((unsigned)nmin), lognmax = ilog2((unsigned)nmax);
@@ -445,7 +445,7 @@ bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluste
         for (int i = 0; i < no; i++) {
             if (cluster_req > 0 && order[i] != cluster_req)
                 continue;
-            if (fused2_config(dbl, kerr, fmax, lognmax, order[i], threads_req, out)) {
+            if (fused2_config(dbl, nl, fmax, lognmax, order[i], threads_req, out)) {
                 out->rt_per_launch = rtpl_req > 0 ? rtpl_req : 64;
                 return true;
             }
@@ -475,7 +475,7 @@ bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluste
             if (!cluster_launchable(dbl, C, sm))
                 break;
             best.kernel = 1;
-            best.kerr = kerr; // the generic kernel branches on it at run time
+            best.nl = nl; // the generic kernel branches on the flags at run time
             best.cluster = C;
             best.threads = kFusedThreads;
             best.rt_per_launch = rtpl_req > 0 ? rtpl_req : 64;

@@ -7,23 +7,23 @@
 namespace opo {
 namespace {
 
-int dispatch(int op, bool ip, bool kr, bool dbl, int F, int logn, const InstDesc *dd, int count,
+int dispatch(int op, bool ip, int nl, bool dbl, int F, int logn, const InstDesc *dd, int count,
              int C, int threads, size_t sm, bool ds, int r_base, int chunk, int last,
              cudaStream_t s)
 {
     if (dbl)
-        return F == 3 ? f2::dispatch_f64_f3(op, ip, kr, logn, dd, count, C, threads, sm, ds, r_base,
+        return F == 3 ? f2::dispatch_f64_f3(op, ip, nl, logn, dd, count, C, threads, sm, ds, r_base,
                                             chunk, last, s)
-                      : f2::dispatch_f64_f2(op, ip, kr, logn, dd, count, C, threads, sm, ds, r_base,
+                      : f2::dispatch_f64_f2(op, ip, nl, logn, dd, count, C, threads, sm, ds, r_base,
                                             chunk, last, s);
-    return F == 3 ? f2::dispatch_f32_f3(op, ip, kr, logn, dd, count, C, threads, sm, ds, r_base,
+    return F == 3 ? f2::dispatch_f32_f3(op, ip, nl, logn, dd, count, C, threads, sm, ds, r_base,
                                         chunk, last, s)
-                  : f2::dispatch_f32_f2(op, ip, kr, logn, dd, count, C, threads, sm, ds, r_base,
+                  : f2::dispatch_f32_f2(op, ip, nl, logn, dd, count, C, threads, sm, ds, r_base,
                                         chunk, last, s);
 }
 
 // In-place variant: X and Y only, dispersion factors from L2.
-bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out)
+bool ip_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
     if (logn < 12 || logn > 16 || (logn == 16 && dbl))
         return false;
@@ -48,14 +48,14 @@ bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, Fused
     size_t sm = el * csz + 32 * kNslot * sizeof(double);
     if (sm > 227 * 1024)
         return false;
-    if (dispatch(1, true, kr, dbl, F, logn, nullptr, 0, C, threads, sm, false, 0, 0, 0, nullptr) < 1)
+    if (dispatch(1, true, nl, dbl, F, logn, nullptr, 0, C, threads, sm, false, 0, 0, 0, nullptr) < 1)
         return false;
     out->cluster = C;
     out->threads = threads;
     out->disp_in_smem = false;
     out->smem = sm;
     out->kernel = 3;
-    out->kerr = kr;
+    out->nl = nl;
     return true;
 }
 
@@ -63,7 +63,7 @@ bool ip_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, Fused
 
 namespace {
 
-bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_req,
+bool three_buffer_config(bool dbl, int nl, int F, int logn, int C, int threads_req,
                          FusedCfg *out)
 {
     const int LP = logn / 2, LQ = logn - LP;
@@ -92,7 +92,7 @@ bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_
         size_t sm = el * csz + 32 * kNslot * sizeof(double);
         if (sm > 227 * 1024)
             continue;
-        if (dispatch(1, false, kr, dbl, F, logn, nullptr, 0, C, threads, sm, ds == 1, 0, 0, 0,
+        if (dispatch(1, false, nl, dbl, F, logn, nullptr, 0, C, threads, sm, ds == 1, 0, 0, 0,
                      nullptr) < 1)
             continue;
         out->cluster = C;
@@ -100,7 +100,7 @@ bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_
         out->disp_in_smem = ds == 1;
         out->smem = sm;
         out->kernel = 2;
-        out->kerr = kr;
+        out->nl = nl;
         return true;
     }
     return false;
@@ -113,13 +113,13 @@ bool three_buffer_config(bool dbl, bool kr, int F, int logn, int C, int threads_
 // points per CTA, so where both fit it usually packs two CTAs per SM); on a
 // tie the three-buffer form, which keeps the dispersion factors in shared
 // memory.
-bool fused2_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out)
+bool fused2_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
     if (logn < 12 || logn > 16 || (logn == 16 && dbl))
         return false;
     FusedCfg a, b;
-    const bool ok_a = three_buffer_config(dbl, kr, F, logn, C, threads_req, &a);
-    const bool ok_b = ip_config(dbl, kr, F, logn, C, threads_req, &b);
+    const bool ok_a = three_buffer_config(dbl, nl, F, logn, C, threads_req, &a);
+    const bool ok_b = ip_config(dbl, nl, F, logn, C, threads_req, &b);
     if (!ok_a && !ok_b)
         return false;
     if (ok_a && ok_b) {
@@ -134,14 +134,14 @@ bool fused2_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, F
 
 int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg)
 {
-    return dispatch(1, cfg.kernel == 3, cfg.kerr, dbl, F, logn, nullptr, 0, cfg.cluster,
+    return dispatch(1, cfg.kernel == 3, cfg.nl, dbl, F, logn, nullptr, 0, cfg.cluster,
                     cfg.threads, cfg.smem, cfg.disp_in_smem, 0, 0, 0, nullptr);
 }
 
 int fused2_launch(bool dbl, int F, int logn, const InstDesc *dd, int count, const FusedCfg &cfg,
                   int r_base, int chunk, int last, cudaStream_t s)
 {
-    return dispatch(0, cfg.kernel == 3, cfg.kerr, dbl, F, logn, dd, count, cfg.cluster,
+    return dispatch(0, cfg.kernel == 3, cfg.nl, dbl, F, logn, dd, count, cfg.cluster,
                     cfg.threads, cfg.smem, cfg.disp_in_smem, r_base, chunk, last, s);
 }
 

@@ -84,12 +84,14 @@ constexpr int f2_col_a2(int LP) { return LP == 8 ? 5 : (LP + 1) / 2; }
 template <class T, bool IP, int LP>
 constexpr int kF2MaxThreadsL = LP >= 8 ? 384 : kF2MaxThreads<T, IP>;
 
-// KR: the Kerr (chi(3)) terms are part of the nonlinear step (a separate
-// instantiation, so that the chi(2)-only kernel keeps its registers and code)
-template <class T, int F, int LP, int LQ, bool IP, bool KR>
+// NL: the nonlinear-step variant (kNlChi2, kNlKerr, kNlChi2NoDk), each a
+// separate instantiation so that every kernel carries only the arithmetic
+// (and the registers) its instances need
+template <class T, int F, int LP, int LQ, bool IP, int NL>
 __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     k_fused2(const InstDesc *__restrict__ descs, int r_base, int M, int write_out, int disp_smem)
 {
+    constexpr bool KR = NL == kNlKerr;
     using V = cv<T>;
     constexpr int P = 1 << LP, Q = 1 << LQ, LN = LP + LQ, N = 1 << LN;
     constexpr int A2 = f2_col_a2(LP), A1 = LP - A2; // columns [Ra1, Ra2]
@@ -243,6 +245,27 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
         ekz = sCry[k].ekz;
     };
 
+    // ---- one RK4 half step (Sec. 2.2) at each of a block-A item's Ra1 points:
+    // without any phase-factor products in the dk = 0 variant, else with them
+    // predicated on the crystal's flag
+    auto rk4_item = [&](V (&v)[F][Ra1], V e0, V e1, V e2) {
+        constexpr int EM = NL == kNlChi2NoDk ? 0 : 2;
+#pragma unroll
+        for (int r = 0; r < Ra1; r++) {
+            V y[F];
+#pragma unroll
+            for (int f = 0; f < F; f++)
+                y[f] = v[f][r];
+            if constexpr (kerr)
+                rk4_point_kerr_e<F, EM>(y, e0, e1, e2, kap, h, use_e, sCry[kcur].G);
+            else
+                rk4_point_e<F, EM>(y, e0, e1, e2, kap, h, use_e);
+#pragma unroll
+            for (int f = 0; f < F; f++)
+                v[f][r] = y[f];
+        }
+    };
+
     // ---- block A: shared by every z-step boundary
     // mode 0: first round trip of the launch, input from global memory
     // mode 1: interior z-step boundary
@@ -316,22 +339,8 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 }
             }
             // time domain: v[f][r] at n1 = j + r Ra2
-            if constexpr (mode == 1 || mode == 2 || mode == 5) {
-#pragma unroll
-                for (int r = 0; r < Ra1; r++) {
-                    V y[F];
-#pragma unroll
-                    for (int f = 0; f < F; f++)
-                        y[f] = v[f][r];
-                    if constexpr (kerr)
-                        rk4_point_kerr<F>(y, e0a, e1a, e2a, kap, h, use_e, sCry[kcur].G);
-                    else
-                        rk4_point<F>(y, e0a, e1a, e2a, kap, h, use_e);
-#pragma unroll
-                    for (int f = 0; f < F; f++)
-                        v[f][r] = y[f];
-                }
-            }
+            if constexpr (mode == 1 || mode == 2 || mode == 5)
+                rk4_item(v, e0a, e1a, e2a);
             if constexpr (mode == 2) {
 #pragma unroll
                 for (int r = 0; r < Ra1; r++) {
@@ -390,42 +399,19 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 // entry of a round trip, then its first RK4 half step
 #pragma unroll
                 for (int r = 0; r < Ra1; r++) {
-                    V y[F];
-#pragma unroll
-                    for (int f = 0; f < F; f++)
-                        y[f] = v[f][r];
                     // the input pump replaces a non-resonant pump and is added
                     // to a resonant one; non-resonant s/i restart from zero
                     const int g = gtime(j + r * Ra2, b);
                     const V pin = dg.ns.on ? ns_pump_at<T>(dg.ns, g, m_cav + 1) : gPump[g];
-                    y[0] = (resmask & 1u) ? cadd(y[0], pin) : pin;
+                    v[0][r] = (resmask & 1u) ? cadd(v[0][r], pin) : pin;
 #pragma unroll
                     for (int f = 1; f < F; f++)
                         if (!(resmask & (1u << f)))
-                            y[f] = cmk<V>((T)0, (T)0);
-                    if constexpr (kerr)
-                        rk4_point_kerr<F>(y, e0b, e1b, e2b, kap, h, use_e, sCry[kcur].G);
-                    else
-                        rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
-#pragma unroll
-                    for (int f = 0; f < F; f++)
-                        v[f][r] = y[f];
+                            v[f][r] = cmk<V>((T)0, (T)0);
                 }
+                rk4_item(v, e0b, e1b, e2b);
             } else if constexpr (mode == 1 || mode == 6) {
-#pragma unroll
-                for (int r = 0; r < Ra1; r++) {
-                    V y[F];
-#pragma unroll
-                    for (int f = 0; f < F; f++)
-                        y[f] = v[f][r];
-                    if constexpr (kerr)
-                        rk4_point_kerr<F>(y, e0b, e1b, e2b, kap, h, use_e, sCry[kcur].G);
-                    else
-                        rk4_point<F>(y, e0b, e1b, e2b, kap, h, use_e);
-#pragma unroll
-                    for (int f = 0; f < F; f++)
-                        v[f][r] = y[f];
-                }
+                rk4_item(v, e0b, e1b, e2b);
             }
             // forward column stage 1: radix Ra1, Ns = 1, outputs at j Ra1 + r
             if constexpr (mode != 5) {
@@ -562,7 +548,10 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     };
 
     // ---- block B: forward row stage 2, spectral factor, inverse row stage 1
-    auto block_b = [&](bool cav, double *acc, int kc) {
+    // cav (compile time): the cavity visit (GDD/delay factor, spectrum sums)
+    // instead of a z-step's dispersion factor
+    auto block_b = [&](auto cav_tag, double *acc, int kc) {
+        constexpr bool cav = decltype(cav_tag)::value;
         const int items = F * Pc * Rb1;
         const V *Dk = sCry[kc].D; // dispersion factors of crystal kc
         const bool dsm = disp_smem && kc == 0;
@@ -736,13 +725,13 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     };
 
     // forward transform (after block A), frequency visit, inverse up to S
-    auto middle = [&](bool cav, double *acc, int kc) {
+    auto middle = [&](auto cav_tag, double *acc, int kc) {
         __syncthreads();
         phase2();
         cluster.sync();
         phase3();
         __syncthreads();
-        block_b(cav, acc, kc);
+        block_b(cav_tag, acc, kc);
         __syncthreads();
         phase5();
         cluster.sync();
@@ -771,7 +760,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
         // is re-read from shared memory.
         int jz = 0;
         while (kcur + 1 < ncry || jz + 1 < sCry[kcur].nz) {
-            middle(false, dummy, kcur);
+            middle(std::false_type{}, dummy, kcur);
             if (jz + 1 < sCry[kcur].nz) {
                 block_a(M1{}, 4 * jz + 2, 4 * (jz + 1), 0, true, false, dummy);
                 jz++;
@@ -783,10 +772,10 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 jz = 0;
             }
         }
-        middle(false, dummy, kcur);
+        middle(std::false_type{}, dummy, kcur);
         double acc[kNslot] = {0, 0, 0, 0, 0};
         block_a(M2{}, 4 * jz + 2, 0, slot, true, write_out && r == M - 1, acc);
-        middle(true, acc, 0);
+        middle(std::true_type{}, acc, 0);
         block_reduce5(acc, red);
         if (threadIdx.x == 0) {
             double *o = obs + (slot * C + c) * kNslot;
@@ -800,11 +789,11 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     }
 }
 
-template <class T, int F, int LP, int LQ, bool IP, bool KR>
+template <class T, int F, int LP, int LQ, bool IP, int NL>
 int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool disp_smem,
              int r_base, int chunk, int last, cudaStream_t s)
 {
-    auto kern = k_fused2<T, F, LP, LQ, IP, KR>;
+    auto kern = k_fused2<T, F, LP, LQ, IP, NL>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t lc = {};
@@ -823,10 +812,10 @@ int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool 
     return e == cudaSuccess ? OPO_OK : OPO_E_CUDA;
 }
 
-template <class T, int F, int LP, int LQ, bool IP, bool KR>
+template <class T, int F, int LP, int LQ, bool IP, int NL>
 int max_active_t(int C, int threads, size_t sm)
 {
-    auto kern = k_fused2<T, F, LP, LQ, IP, KR>;
+    auto kern = k_fused2<T, F, LP, LQ, IP, NL>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t lc = {};
@@ -849,46 +838,47 @@ int max_active_t(int C, int threads, size_t sm)
 }
 
 // Launch (op 0) or occupancy query (op 1) of every instantiated size for one
-// precision and field count; ip selects the in-place variant, kr the
-// instantiation with the Kerr terms.  The chi(2)-only and the
-// Kerr instantiations of a precision and field count are defined in two
-// translation units (opo_fused2_<prec>_<F>.cu and ..._kerr.cu) that compile in
-// parallel.
+// precision and field count; ip selects the in-place variant, nl the
+// nonlinear-step variant.  The variants of a precision and field count are
+// defined in separate translation units (opo_fused2_<prec>_<F>.cu, ..._kerr.cu
+// and, single precision only, ..._nodk.cu) that compile in parallel.
 #define OPO_F2_DISPATCH_DECL(NAME)                                                               \
-    int NAME(int op, bool ip, bool kr, int logn, const InstDesc *dd, int count, int C,          \
+    int NAME(int op, bool ip, int nl, int logn, const InstDesc *dd, int count, int C,            \
              int threads, size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
-#define OPO_F2_DISPATCH_KR_DECL(NAME)                                                            \
-    int NAME(int op, bool ip, int logn, const InstDesc *dd, int count, int C, int threads,      \
+#define OPO_F2_DISPATCH_NL_DECL(NAME)                                                            \
+    int NAME(int op, bool ip, int logn, const InstDesc *dd, int count, int C, int threads,       \
              size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
 OPO_F2_DISPATCH_DECL(dispatch_f32_f3);
 OPO_F2_DISPATCH_DECL(dispatch_f32_f2);
 OPO_F2_DISPATCH_DECL(dispatch_f64_f3);
 OPO_F2_DISPATCH_DECL(dispatch_f64_f2);
-OPO_F2_DISPATCH_KR_DECL(dispatch_f32_f3_kerr);
-OPO_F2_DISPATCH_KR_DECL(dispatch_f32_f2_kerr);
-OPO_F2_DISPATCH_KR_DECL(dispatch_f64_f3_kerr);
-OPO_F2_DISPATCH_KR_DECL(dispatch_f64_f2_kerr);
+OPO_F2_DISPATCH_NL_DECL(dispatch_f32_f3_kerr);
+OPO_F2_DISPATCH_NL_DECL(dispatch_f32_f2_kerr);
+OPO_F2_DISPATCH_NL_DECL(dispatch_f64_f3_kerr);
+OPO_F2_DISPATCH_NL_DECL(dispatch_f64_f2_kerr);
+OPO_F2_DISPATCH_NL_DECL(dispatch_f32_f3_nodk);
+OPO_F2_DISPATCH_NL_DECL(dispatch_f32_f2_nodk);
 
-#define OPO_F2_ONE(T, F, LP, LQ, IP, KR)                                                         \
-    return op == 0 ? launch_t<T, F, LP, LQ, IP, KR>(dd, count, C, threads, sm, ds, r_base,      \
+#define OPO_F2_ONE(T, F, LP, LQ, IP, NL)                                                         \
+    return op == 0 ? launch_t<T, F, LP, LQ, IP, NL>(dd, count, C, threads, sm, ds, r_base,       \
                                                     chunk, last, s)                              \
-                   : max_active_t<T, F, LP, LQ, IP, KR>(C, threads, sm)
+                   : max_active_t<T, F, LP, LQ, IP, NL>(C, threads, sm)
 
-// every size for one (T, F, KR)
-#define OPO_F2_SIZES(T, F, KR)                                                                   \
+// every size for one (T, F, NL)
+#define OPO_F2_SIZES(T, F, NL)                                                                   \
     if (ip) {                                                                                    \
         switch (logn) {                                                                          \
         case 12:                                                                                 \
-            OPO_F2_ONE(T, F, 6, 6, true, KR);                                                    \
+            OPO_F2_ONE(T, F, 6, 6, true, NL);                                                    \
         case 13:                                                                                 \
-            OPO_F2_ONE(T, F, 6, 7, true, KR);                                                    \
+            OPO_F2_ONE(T, F, 6, 7, true, NL);                                                    \
         case 14:                                                                                 \
-            OPO_F2_ONE(T, F, 7, 7, true, KR);                                                    \
+            OPO_F2_ONE(T, F, 7, 7, true, NL);                                                    \
         case 15:                                                                                 \
-            OPO_F2_ONE(T, F, 7, 8, true, KR);                                                    \
+            OPO_F2_ONE(T, F, 7, 8, true, NL);                                                    \
         case 16:                                                                                 \
             if constexpr (sizeof(T) == 4) {                                                      \
-                OPO_F2_ONE(T, F, 8, 8, true, KR);                                                \
+                OPO_F2_ONE(T, F, 8, 8, true, NL);                                                \
             }                                                                                    \
             return op == 0 ? OPO_E_UNSUPPORTED : 0;                                              \
         default:                                                                                 \
@@ -897,36 +887,55 @@ OPO_F2_DISPATCH_KR_DECL(dispatch_f64_f2_kerr);
     }                                                                                            \
     switch (logn) {                                                                              \
     case 12:                                                                                     \
-        OPO_F2_ONE(T, F, 6, 6, false, KR);                                                       \
+        OPO_F2_ONE(T, F, 6, 6, false, NL);                                                       \
     case 13:                                                                                     \
-        OPO_F2_ONE(T, F, 6, 7, false, KR);                                                       \
+        OPO_F2_ONE(T, F, 6, 7, false, NL);                                                       \
     case 14:                                                                                     \
-        OPO_F2_ONE(T, F, 7, 7, false, KR);                                                       \
+        OPO_F2_ONE(T, F, 7, 7, false, NL);                                                       \
     case 15:                                                                                     \
-        OPO_F2_ONE(T, F, 7, 8, false, KR);                                                       \
+        OPO_F2_ONE(T, F, 7, 8, false, NL);                                                       \
     case 16:                                                                                     \
         if constexpr (sizeof(T) == 4) {                                                          \
-            OPO_F2_ONE(T, F, 8, 8, false, KR);                                                   \
+            OPO_F2_ONE(T, F, 8, 8, false, NL);                                                   \
         }                                                                                        \
         return op == 0 ? OPO_E_UNSUPPORTED : 0;                                                  \
     default:                                                                                     \
         return op == 0 ? OPO_E_UNSUPPORTED : 0;                                                  \
     }
 
-// the chi(2)-only sizes, and the entry point that forwards Kerr requests
+// the general chi(2) sizes, and the entry point that forwards the other
+// variants to their translation units (FP64 has no dk = 0 variant)
 #define OPO_F2_DISPATCH_DEF(NAME, T, F)                                                          \
     OPO_F2_DISPATCH_DECL(NAME)                                                                   \
     {                                                                                            \
-        if (kr)                                                                                  \
-            return NAME##_kerr(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk,      \
+        if (nl == kNlKerr)                                                                       \
+            return NAME##_kerr(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk,       \
                                last, s);                                                         \
-        OPO_F2_SIZES(T, F, false)                                                                \
+        OPO_F2_SIZES(T, F, kNlChi2)                                                              \
+    }
+
+#define OPO_F2_DISPATCH_DEF_NODK(NAME, T, F)                                                     \
+    OPO_F2_DISPATCH_DECL(NAME)                                                                   \
+    {                                                                                            \
+        if (nl == kNlKerr)                                                                       \
+            return NAME##_kerr(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk,       \
+                               last, s);                                                         \
+        if (nl == kNlChi2NoDk)                                                                   \
+            return NAME##_nodk(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk,       \
+                               last, s);                                                         \
+        OPO_F2_SIZES(T, F, kNlChi2)                                                              \
     }
 
 #define OPO_F2_DISPATCH_KERR_DEF(NAME, T, F)                                                     \
-    OPO_F2_DISPATCH_KR_DECL(NAME##_kerr)                                                         \
+    OPO_F2_DISPATCH_NL_DECL(NAME##_kerr)                                                         \
     {                                                                                            \
-        OPO_F2_SIZES(T, F, true)                                                                 \
+        OPO_F2_SIZES(T, F, kNlKerr)                                                              \
+    }
+
+#define OPO_F2_DISPATCH_NODK_DEF(NAME, T, F)                                                     \
+    OPO_F2_DISPATCH_NL_DECL(NAME##_nodk)                                                         \
+    {                                                                                            \
+        OPO_F2_SIZES(T, F, kNlChi2NoDk)                                                          \
     }
 
 } // namespace f2

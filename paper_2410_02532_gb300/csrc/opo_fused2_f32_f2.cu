@@ -3,6 +3,6 @@
 
 namespace opo {
 namespace f2 {
-OPO_F2_DISPATCH_DEF(dispatch_f32_f2, float, 2)
+OPO_F2_DISPATCH_DEF_NODK(dispatch_f32_f2, float, 2)
 } // namespace f2
 } // namespace opo

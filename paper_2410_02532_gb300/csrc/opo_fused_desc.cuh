@@ -87,7 +87,7 @@ void fill_desc(InstDesc &d, const opo_ctx *c);
 
 // opo_fused2.cu: the size-specialised kernel (N = 2^12 .. 2^15, one size and
 // field count per launch).
-bool fused2_config(bool dbl, bool kr, int F, int logn, int C, int threads_req, FusedCfg *out);
+bool fused2_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedCfg *out);
 int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg);
 int fused2_launch(bool dbl, int F, int logn, const InstDesc *dd, int count, const FusedCfg &cfg,
                   int r_base, int chunk, int last, cudaStream_t s);

@@ -58,9 +58,16 @@ struct CrystalState {
     int ekz_cap = 0;
 };
 
+// Nonlinear-step variants of the size-specialised fused kernel, each its own
+// instantiation: chi(2) with the phase-mismatch factors switched by a runtime
+// flag per crystal; chi(2) plus the Kerr terms; chi(2) where dk = 0 in every
+// crystal (no phase factors at all: the RK4 step without its predicated
+// products).
+constexpr int kNlChi2 = 0, kNlKerr = 1, kNlChi2NoDk = 2;
+
 struct FusedCfg {
     int kernel = 1;      // 1: generic, 2: size-specialised, 3: size-specialised in place
-    bool kerr = false;   // instances carry the chi(3) terms (kernels 2, 3 instantiate it)
+    int nl = 0;          // kNl* variant (kernels 2, 3 instantiate each)
     int cluster;         // CTAs per instance
     int threads;         // threads per CTA
     int rt_per_launch;   // round trips per launch
@@ -79,6 +86,7 @@ struct opo_ctx {
     opo::CryDesc h_cry[OPO_MAX_CRYSTALS]; // host copy of the descriptors
     opo::CryDesc *d_cry = nullptr;        // their device copy (kMaxCry entries)
     bool kerr_any = false;                // some crystal has Kerr terms
+    bool dk_any = false;                  // some crystal has dk != 0
     opo_cavity cavity;
     bool have_crystal = false, have_cavity = false;
     int device = 0;
@@ -146,10 +154,17 @@ int plain_pass_raw(void *fields, void *scratch, const void *tw, const void *disp
 // crystal; false (all zero) when its n2 is 0.
 bool kerr_coefficients(const opo_crystal &k, int F, double g[9]);
 
+// the size-specialised kernel variant an instance needs (kNl*)
+inline int nl_variant(const opo_ctx *c)
+{
+    return c->kerr_any ? kNlKerr : (c->dk_any ? kNlChi2 : kNlChi2NoDk);
+}
+
 // opo_fused.cu: a cluster configuration able to hold instances with up to
-// fmax fields and nmin..nmax points (false if none fits or can launch).
+// fmax fields and nmin..nmax points and nonlinear-step variant nl (false if
+// none fits or can launch).
 bool fused_config(size_t csz, int fmin, int fmax, int nmin, int nmax, int cluster_req,
-                  int rtpl_req, int threads_req, bool kerr, FusedCfg *out);
+                  int rtpl_req, int threads_req, int nl, FusedCfg *out);
 int fused_max_active(bool dbl, int F, int n, const FusedCfg &cfg);
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s);
 
