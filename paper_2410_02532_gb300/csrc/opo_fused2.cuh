@@ -224,6 +224,21 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     };
     auto CI = [=](int f, int n1, int b) { return IP ? cidx_ip(f, n1, b) : cidx(f, n1, b); };
     auto RI = [=](int f, int row, int e) { return IP ? ridx_ip(f, row, e) : ridx(f, row, e); };
+    // IP accesses of one work item touch the elements e0 | x of one column
+    // (row), x = r R a compile-time constant with bits disjoint from e0.  The
+    // swizzle is linear over the bits of the element index, so that element
+    // sits at the byte offset (a0 ^ lo(x)) + hi(x) from the first one's
+    // offset a0: one logic operation per access, the rest an immediate.
+    // (Buffer and column/row starts are multiples of 128 bytes, so the XOR
+    // stays within the swizzled bits.)
+    auto ipo = [&](const V *buf, int i0) -> unsigned {
+        return (unsigned)((const unsigned char *)(buf + i0) - smem_raw);
+    };
+    auto ipx = [&](unsigned a0, int x) -> V & {
+        const unsigned lo = (unsigned)(((x ^ (x >> SW)) & SWM) * (int)sizeof(V));
+        const unsigned hi = (unsigned)((x & ~SWM) * (int)sizeof(V));
+        return *reinterpret_cast<V *>(smem_raw + ((a0 ^ lo) + hi));
+    };
     auto gtime = [=](int n1, int b) { return (n1 << LQ) + (c << logQc) + b; };
     auto twN = [&](unsigned a) {
         a &= (unsigned)(N - 1);
@@ -313,10 +328,18 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             } else {
                 const V *src = IP ? X : S;
 #pragma unroll
-                for (int f = 0; f < F; f++)
+                for (int f = 0; f < F; f++) {
+                    if constexpr (IP) {
+                        const unsigned a0 = ipo(X, CI(f, j, b));
 #pragma unroll
-                    for (int r = 0; r < Ra1; r++)
-                        v[f][r] = src[CI(f, j + r * Ra2, b)];
+                        for (int r = 0; r < Ra1; r++)
+                            v[f][r] = ipx(a0, r * Ra2);
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < Ra1; r++)
+                            v[f][r] = src[CI(f, j + r * Ra2, b)];
+                    }
+                }
             }
         };
         // own: this lane owns work item u (lanes past the end of the last
@@ -428,16 +451,32 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 // time domain, back where the values came from
                 V *dst = IP ? X : S;
 #pragma unroll
-                for (int f = 0; f < F; f++)
+                for (int f = 0; f < F; f++) {
+                    if constexpr (IP) {
+                        const unsigned a0 = ipo(X, CI(f, j, b));
 #pragma unroll
-                    for (int r = 0; r < Ra1; r++)
-                        dst[CI(f, j + r * Ra2, b)] = v[f][r];
+                        for (int r = 0; r < Ra1; r++)
+                            ipx(a0, r * Ra2) = v[f][r];
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < Ra1; r++)
+                            dst[CI(f, j + r * Ra2, b)] = v[f][r];
+                    }
+                }
             } else {
 #pragma unroll
-                for (int f = 0; f < F; f++)
+                for (int f = 0; f < F; f++) {
+                    if constexpr (IP) {
+                        const unsigned a0 = ipo(X, CI(f, j * Ra1, b));
 #pragma unroll
-                    for (int r = 0; r < Ra1; r++)
-                        X[CI(f, j * Ra1 + r, b)] = v[f][r];
+                        for (int r = 0; r < Ra1; r++)
+                            ipx(a0, r) = v[f][r];
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < Ra1; r++)
+                            X[CI(f, j * Ra1 + r, b)] = v[f][r];
+                    }
+                }
             }
         };
         if constexpr (IP && mode != 0) {
@@ -481,9 +520,16 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             const int rest = u >> logQc;
             const int j = rest & (Ra1 - 1), f = rest >> A1;
             V v[Ra2];
+            if constexpr (IP) {
+                const unsigned a0 = ipo(X, CI(f, j, b));
 #pragma unroll
-            for (int r = 0; r < Ra2; r++)
-                v[r] = X[CI(f, j + r * Ra1, b)];
+                for (int r = 0; r < Ra2; r++)
+                    v[r] = ipx(a0, r * Ra1);
+            } else {
+#pragma unroll
+                for (int r = 0; r < Ra2; r++)
+                    v[r] = X[CI(f, j + r * Ra1, b)];
+            }
 #pragma unroll
             for (int r = 1; r < Ra2; r++)
                 v[r] = cmul(v[r], tw2[r * Ra1 + j]);
@@ -519,15 +565,17 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 int j, row, f;
                 V v[Rb1];
                 dec(u, j, row, f);
+                const unsigned a0 = ipo(Y, RI(f, row, j));
 #pragma unroll
                 for (int r = 0; r < Rb1; r++)
-                    v[r] = Y[RI(f, row, j + r * Rb2)];
+                    v[r] = ipx(a0, r * Rb2);
                 dft_r<Rb1, -1>(v);
                 __syncwarp();
                 if (have) {
+                    const unsigned a1 = ipo(Y, RI(f, row, j * Rb1));
 #pragma unroll
                     for (int r = 0; r < Rb1; r++)
-                        Y[RI(f, row, j * Rb1 + r)] = v[r];
+                        ipx(a1, r) = v[r];
                 }
                 __syncwarp();
             }
@@ -565,9 +613,16 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
         auto load = [&](int u, V (&v)[Rb2]) {
             int j, row, f;
             decode(u, j, row, f);
+            if constexpr (IP) {
+                const unsigned a0 = ipo(Y, RI(f, row, j));
 #pragma unroll
-            for (int r = 0; r < Rb2; r++)
-                v[r] = src[RI(f, row, j + r * Rb1)];
+                for (int r = 0; r < Rb2; r++)
+                    v[r] = ipx(a0, r * Rb1);
+            } else {
+#pragma unroll
+                for (int r = 0; r < Rb2; r++)
+                    v[r] = src[RI(f, row, j + r * Rb1)];
+            }
         };
         auto finish = [&](int u, V (&v)[Rb2], bool own) {
             int j, row, f;
@@ -608,9 +663,16 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
         auto store = [&](int u, V (&v)[Rb2]) {
             int j, row, f;
             decode(u, j, row, f);
+            if constexpr (IP) {
+                const unsigned a0 = ipo(Y, RI(f, row, j * Rb2));
 #pragma unroll
-            for (int r = 0; r < Rb2; r++)
-                Y[RI(f, row, j * Rb2 + r)] = v[r];
+                for (int r = 0; r < Rb2; r++)
+                    ipx(a0, r) = v[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < Rb2; r++)
+                    Y[RI(f, row, j * Rb2 + r)] = v[r];
+            }
         };
         if constexpr (IP) {
 #pragma unroll 1
@@ -657,9 +719,16 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 f = rest >> logPc;
             }
             V v[Rb1];
+            if constexpr (IP) {
+                const unsigned a0 = ipo(Y, RI(f, row, j));
 #pragma unroll
-            for (int r = 0; r < Rb1; r++)
-                v[r] = Y[RI(f, row, j + r * Rb2)];
+                for (int r = 0; r < Rb1; r++)
+                    v[r] = ipx(a0, r * Rb2);
+            } else {
+#pragma unroll
+                for (int r = 0; r < Rb1; r++)
+                    v[r] = Y[RI(f, row, j + r * Rb2)];
+            }
 #pragma unroll
             for (int r = 1; r < Rb1; r++) {
                 V w = tw5[r * Rb2 + j];
@@ -695,15 +764,17 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 const int rest = u >> A1;
                 const int b = rest & (Qc - 1), f = rest >> logQc;
                 V v[Ra2];
+                const unsigned a0 = ipo(X, cidx_ip(f, j, b));
 #pragma unroll
                 for (int r = 0; r < Ra2; r++)
-                    v[r] = X[cidx_ip(f, j + r * Ra1, b)];
+                    v[r] = ipx(a0, r * Ra1);
                 dft_r<Ra2, 1>(v);
                 __syncwarp();
                 if (have) {
+                    const unsigned a1 = ipo(X, cidx_ip(f, j * Ra2, b));
 #pragma unroll
                     for (int r = 0; r < Ra2; r++)
-                        X[cidx_ip(f, j * Ra2 + r, b)] = v[r];
+                        ipx(a1, r) = v[r];
                 }
                 __syncwarp();
             }
