@@ -245,6 +245,38 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
         return cmul(twHi[a >> LS], twLo[a & ((1u << LS) - 1)]);
     };
 
+    // ---- IP pushes: for the unrolled position r of a phase-2 (phase-5) item,
+    // the address in the owner CTA of the start of the destination row
+    // (column) group and the swizzle term of that group's row (column)
+    // number; the item's own part of the destination index is XORed with the
+    // latter and added to the former (row and swizzle are both linear in the
+    // bits of the row (column) index).  Holds when a CTA owns at least one
+    // butterfly group along the destination direction (Pc >= Ra1,
+    // Qc >= Rb2).  Taken for clusters of one or two CTAs (+5% at 2^12, +2.5%
+    // at 2^13); with more destinations the per-element table loads cost more
+    // than the index arithmetic they replace (-1 to -3% at 2^14..2^16), and
+    // the pushes compute the index per element.
+    struct __align__(16) PushEnt {
+        unsigned char *p;
+        unsigned x;
+    };
+    __shared__ PushEnt sPush2[IP ? Ra2 : 1], sPush5[IP ? Rb1 : 1];
+    const bool tab2 = IP && C <= 2 && Pc >= Ra1, tab5 = IP && C <= 2 && Qc >= Rb2;
+    if constexpr (IP) {
+        if (tab2 && (int)threadIdx.x < Ra2) {
+            const int k1 = (int)threadIdx.x * Ra1, R = k1 & (Pc - 1);
+            V *dY = cluster.map_shared_rank(Y, (unsigned)(k1 >> logPc));
+            sPush2[threadIdx.x].p = (unsigned char *)(dY + (R << LQ));
+            sPush2[threadIdx.x].x = (unsigned)(sizeof(V) * perm(R));
+        }
+        if (tab5 && (int)threadIdx.x < Rb1) {
+            const int n2 = (int)threadIdx.x * Rb2, B = n2 & (Qc - 1);
+            V *dX = cluster.map_shared_rank(X, (unsigned)(n2 >> logQc));
+            sPush5[threadIdx.x].p = (unsigned char *)(dX + (B << LP));
+            sPush5[threadIdx.x].x = (unsigned)(sizeof(V) * perm(B));
+        }
+    }
+
     // ---- constants of the crystal being passed (registers, as for one
     // crystal); set_crystal switches them where the next crystal begins
     T kap[3], h;
@@ -327,6 +359,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 }
             } else {
                 const V *src = IP ? X : S;
+                (void)src;
 #pragma unroll
                 for (int f = 0; f < F; f++) {
                     if constexpr (IP) {
@@ -450,6 +483,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             if constexpr (mode == 5) {
                 // time domain, back where the values came from
                 V *dst = IP ? X : S;
+                (void)dst;
 #pragma unroll
                 for (int f = 0; f < F; f++) {
                     if constexpr (IP) {
@@ -538,11 +572,21 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             // W_N^{n2 k1} for k1 = j + r Ra1: base W_N^{n2 j} times step^r
             const V step = twN((unsigned)(n2 * Ra1));
             V w = twN((unsigned)(n2 * j));
+            if (tab2) {
+                const unsigned a0 = (unsigned)(sizeof(V) * RI(f, j, n2));
 #pragma unroll
-            for (int r = 0; r < Ra2; r++) {
-                const int k1 = j + r * Ra1;
-                rY[k1 >> logPc][RI(f, k1 & (Pc - 1), n2)] = cmul(v[r], w);
-                w = cmul(w, step);
+                for (int r = 0; r < Ra2; r++) {
+                    const PushEnt t = sPush2[r];
+                    *reinterpret_cast<V *>(t.p + (a0 ^ t.x)) = cmul(v[r], w);
+                    w = cmul(w, step);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < Ra2; r++) {
+                    const int k1 = j + r * Ra1;
+                    rY[k1 >> logPc][RI(f, k1 & (Pc - 1), n2)] = cmul(v[r], w);
+                    w = cmul(w, step);
+                }
             }
         }
     };
@@ -604,6 +648,8 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
         const V *Dk = sCry[kc].D; // dispersion factors of crystal kc
         const bool dsm = disp_smem && kc == 0;
         const V *src = IP ? Y : S;
+        (void)dsm;
+        (void)src;
         auto decode = [&](int u, int &j, int &row, int &f) {
             j = u & (Rb1 - 1);
             const int rest = u >> B1;
@@ -632,6 +678,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             // a warp's loads (consecutive j) coalesce; issued before the
             // transform so that their latency overlaps it
             V fac[IP ? Rb2 : 1];
+            (void)fac;
             if constexpr (IP) {
                 const V *tab = (cav ? gGt : Dk) + f * N + (k1 << LQ) + j;
 #pragma unroll
@@ -742,11 +789,21 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             step.y = -step.y;
             V w = twN((unsigned)(k1 * j));
             w.y = -w.y;
+            if (tab5) {
+                const unsigned a0 = (unsigned)(sizeof(V) * CI(f, k1, j));
 #pragma unroll
-            for (int r = 0; r < Rb1; r++) {
-                const int n2 = j + r * Rb2;
-                rX[n2 >> logQc][CI(f, k1, n2 & (Qc - 1))] = cmul(v[r], w);
-                w = cmul(w, step);
+                for (int r = 0; r < Rb1; r++) {
+                    const PushEnt t = sPush5[r];
+                    *reinterpret_cast<V *>(t.p + (a0 ^ t.x)) = cmul(v[r], w);
+                    w = cmul(w, step);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < Rb1; r++) {
+                    const int n2 = j + r * Rb2;
+                    rX[n2 >> logQc][CI(f, k1, n2 & (Qc - 1))] = cmul(v[r], w);
+                    w = cmul(w, step);
+                }
             }
         }
     };
