@@ -34,9 +34,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SSFM field-steps/s at N=2^14 (fused, batched round trips)"
 # (instances, cluster, threads requested) -> DRAM bytes per fused launch of the
-# 2^14 workload (48.13 MB read + 0.91 MB written; threads 0 = the library's
-# default, 512, for this shape)
-PROFILED_SHAPES = {(36, 4, 0): 49.037824e6, (36, 4, 512): 49.037824e6}
+# 2^14 workload, from ncu captures of the current kernel: 4-CTA clusters of
+# 512 threads 48.13 MB read + 1.00 MB written (threads 0 = the library's
+# default, 512, for this shape); 8-CTA clusters of 128 threads 48.11 MB read +
+# 0.66 MB written
+PROFILED_SHAPES = {(36, 4, 0): 49.13152e6, (36, 4, 512): 49.13152e6,
+                   (36, 8, 128): 48.769536e6}
 UNIT = "field-steps/s"
 PEAK_SM_MHZ = 2070.0          # GB300 maximum SM clock
 SMS = 152
