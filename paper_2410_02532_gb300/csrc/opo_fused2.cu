@@ -111,8 +111,8 @@ bool three_buffer_config(bool dbl, int nl, int F, int logn, int C, int threads_r
 // Of the two forms that can run (N, F, C, threads), take the one with more
 // clusters co-resident on the device (the in-place form holds twice the
 // points per CTA, so where both fit it usually packs two CTAs per SM); on a
-// tie the three-buffer form, which keeps the dispersion factors in shared
-// memory.
+// tie the three-buffer form if it keeps the dispersion factors in shared
+// memory, else the in-place form (cheaper addressing, same passes).
 bool fused2_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
     if (logn < 12 || logn > 16 || (logn == 16 && dbl))
@@ -125,7 +125,7 @@ bool fused2_config(bool dbl, int nl, int F, int logn, int C, int threads_req, Fu
     if (ok_a && ok_b) {
         const int na = fused2_max_active(dbl, F, logn, a);
         const int nb = fused2_max_active(dbl, F, logn, b);
-        *out = nb > na ? b : a;
+        *out = (nb > na || (nb == na && !a.disp_in_smem)) ? b : a;
     } else {
         *out = ok_a ? a : b;
     }
