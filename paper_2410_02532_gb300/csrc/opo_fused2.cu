@@ -34,11 +34,6 @@ bool ip_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedC
     const int Qc = (1 << LQ) / C;
     const int nc = (1 << logn) / C;
     const int maxT = dbl ? 256 : (logn >= 16 ? 384 : 512);
-    int threads = threads_req;
-    if (threads == 0) // 2^16: 256 (two block-A items per thread) measured best
-        threads = logn >= 16 ? 256 : std::min(maxT, (F * Qc * (1 << A1) + 31) / 32 * 32);
-    if (threads < 32 || threads > maxT || (threads & 31))
-        return false;
     (void)A2;
     const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
     const int LS = (logn + 1) / 2;
@@ -47,6 +42,19 @@ bool ip_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedC
                 ((1 << logn) >> LS);
     size_t sm = el * csz + 32 * kNslot * sizeof(double);
     if (sm > 227 * 1024)
+        return false;
+    int threads = threads_req;
+    if (threads == 0) {
+        // one phase-2 item per thread; 2^16: 256 (two block-A items per
+        // thread) measured best; three FP32 fields where the shared memory
+        // admits two CTAs per SM: 128, so that the registers admit them too
+        // (2^14 on 8-CTA clusters 93.7 against 64.7 G point-field-steps/s
+        // with 384 threads, 2^15 on 16-CTA clusters 72.3 against 55.8)
+        threads = logn >= 16 ? 256 : std::min(maxT, (F * Qc * (1 << A1) + 31) / 32 * 32);
+        if (!dbl && F == 3 && logn < 16 && 2 * (sm + 1024) <= 228 * 1024)
+            threads = 128;
+    }
+    if (threads < 32 || threads > maxT || (threads & 31))
         return false;
     if (dispatch(1, true, nl, dbl, F, logn, nullptr, 0, C, threads, sm, false, 0, 0, 0, nullptr) < 1)
         return false;
