@@ -36,8 +36,6 @@ template <class V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a
 // of a crystal, one or many instances) round the same.
 __device__ __forceinline__ float fmad_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmad_(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float fadd_(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double fadd_(double a, double b) { return __dadd_rn(a, b); }
 template <class V> __device__ __forceinline__ V cmul(V a, V b)
 {
     return cmk<V>(fmad_(a.x, b.x, -(a.y * b.y)), fmad_(a.x, b.y, a.y * b.x));
