@@ -1,6 +1,9 @@
 """Autotuner for the fused path: picks the launch shape of an instance class.
 
-An instance class is (N, field count, precision).  Candidates are
+An instance class is (N, field count, precision, nonlinear-step variant:
+chi(2) with a phase mismatch somewhere, chi(2) with dk = 0 in every crystal,
+or with the Kerr terms -- the library runs each on its own kernel, and the
+Kerr kernel prefers larger CTAs than the chi(2) ones).  Candidates are
 (cluster size, threads per CTA, round trips per launch); each candidate that
 the library accepts is timed on a batch that fills the GPU (as many
 co-resident clusters as the occupancy query allows) with CUDA events on the
@@ -26,8 +29,19 @@ _cache = {}
 _lock = threading.Lock()
 
 
-def _key(n, nfields, precision):
-    return "%d/%d/%d" % (int(n), int(nfields), int(precision))
+def variant(cfg):
+    """The nonlinear-step variant of an ``OPOConfig``: "kerr" if any crystal
+    has an n2, else "chi2" if any has a phase mismatch, else "chi2_dk0"."""
+    crystals = (cfg,) + tuple(getattr(cfg, "extra_crystals", ()) or ())
+    if any(getattr(k, "n2", 0.0) != 0.0 for k in crystals):
+        return "kerr"
+    if any(getattr(k, "dk", 0.0) != 0.0 for k in crystals):
+        return "chi2"
+    return "chi2_dk0"
+
+
+def _key(n, nfields, precision, var="chi2_dk0"):
+    return "%d/%d/%d/%s" % (int(n), int(nfields), int(precision), var)
 
 
 def load(path):
@@ -48,9 +62,9 @@ def save(path):
     os.replace(tmp, path)
 
 
-def lookup(n, nfields, precision):
+def lookup(n, nfields, precision, var="chi2_dk0"):
     with _lock:
-        return _cache.get(_key(n, nfields, precision))
+        return _cache.get(_key(n, nfields, precision, var))
 
 
 def tune(cfg, precision=opo.OPO_FP32_PH64, device=0, round_trips=2, candidates=None, reps=3):
@@ -62,7 +76,8 @@ def tune(cfg, precision=opo.OPO_FP32_PH64, device=0, round_trips=2, candidates=N
     """
     import torch
 
-    hit = lookup(cfg.n, cfg.nfields, precision)
+    var = variant(cfg)
+    hit = lookup(cfg.n, cfg.nfields, precision, var)
     if hit is not None:
         return hit
     stream = torch.cuda.Stream(device=device)
@@ -120,7 +135,7 @@ def tune(cfg, precision=opo.OPO_FP32_PH64, device=0, round_trips=2, candidates=N
     best = max(ties, key=lambda r: (r["threads"], r["field_steps_per_s"]))
     best = dict(best, candidates=len(results))
     with _lock:
-        _cache[_key(cfg.n, cfg.nfields, precision)] = best
+        _cache[_key(cfg.n, cfg.nfields, precision, var)] = best
     return best
 
 

@@ -19,3 +19,41 @@ def test_instance_bytes_and_work():
     assert serving.instance_bytes(1 << 14, 3, 1) < serving.instance_bytes(1 << 14, 3, 0)
     r = serving.poisson_trace(1, 1.0)[0]
     assert serving.request_work(r) == r.cfg.n * r.cfg.nfields * r.cfg.nz * r.rounds
+
+
+def test_autotune_classes_follow_the_kernel_variant():
+    """The tuner keys a class by the nonlinear-step variant as the library
+    picks its kernel: Kerr terms anywhere, else a phase mismatch anywhere,
+    else the dk = 0 kernel; and its cache round-trips through a JSON file."""
+    import os
+    import tempfile
+
+    from paper_2410_02532_gb300 import autotune as A
+    from paper_2410_02532_gb300 import workloads as W
+
+    base = W.cw_sro_16k()
+    assert base.dk == 0.0 and base.n2 == 0.0
+    assert A.variant(base) == "chi2_dk0"
+    assert A.variant(base.replace(dk=10.0)) == "chi2"
+    assert A.variant(base.replace(n2=2e-19)) == "kerr"
+    assert A.variant(base.replace(dk=10.0, n2=2e-19)) == "kerr"
+    second = W.Crystal(length=1e-3, nz=2, dk=5.0)
+    assert A.variant(base.replace(extra_crystals=(second,))) == "chi2"
+    keys = {A._key(base.n, base.nfields, 1, v) for v in ("chi2", "chi2_dk0", "kerr")}
+    assert len(keys) == 3
+    shape = {"cluster": 4, "threads": 512, "rt_per_launch": 64, "field_steps_per_s": 1.0}
+    with A._lock:
+        A._cache[A._key(base.n, base.nfields, 1, "kerr")] = shape
+    try:
+        assert A.lookup(base.n, base.nfields, 1, "kerr") == shape
+        assert A.lookup(base.n, base.nfields, 1, "chi2_dk0") is None
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "tune.json")
+            A.save(path)
+            with A._lock:
+                A._cache.clear()
+            A.load(path)
+            assert A.lookup(base.n, base.nfields, 1, "kerr") == shape
+    finally:
+        with A._lock:
+            A._cache.clear()
