@@ -300,7 +300,8 @@ def main():
 
     extras = {}
     if not args.skip_extras and rank == 0:
-        # one instance alone: the default (latency-oriented) launch shape
+        # one instance alone, at the default cluster and the fastest of a few
+        # CTA sizes
         extras = single_and_plain(args, opo, W, base, prec, local, torch)
         extras["e2e"] = e2e(args, opo, W, ctxs, batch, base, torch, np)
         extras["batched_sweep"] = sweep_leg(opo, W, prec, local, torch)
