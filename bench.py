@@ -70,7 +70,7 @@ def total_nz(cfg):
 
 
 def flops_per_roundtrip(cfg):
-    """Algorithmic FLOPs of one round trip of one instance (the design doc's model).
+    """Algorithmic FLOPs of one round trip of one instance (the roofline's model).
 
     per point-field per z-step: two FFTs 2 * 5 log2 N, dispersion multiply 6,
     two RK4 half steps 2 * rk4 where rk4 = 58 (3 fields) / 62 (2 fields) per

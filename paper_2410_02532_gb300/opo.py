@@ -247,7 +247,7 @@ def opo_batch_destroy(batch):
 def opo_batch_set_fields(batch, host):
     """host: complex128 array holding every member's F x N fields in batch
     order (a flat array of sum F N values, or anything that flattens to it;
-    a pinned contiguous buffer avoids a staging copy in the driver)."""
+    a pinned contiguous buffer avoids a staging copy in the CUDA runtime)."""
     a = np.ascontiguousarray(host, dtype=np.complex128).reshape(-1)
     _check(lib().opo_batch_set_fields(batch, a.ctypes.data_as(_DP), a.size),
            "opo_batch_set_fields")
