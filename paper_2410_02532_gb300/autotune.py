@@ -67,6 +67,21 @@ def lookup(n, nfields, precision, var="chi2_dk0"):
         return _cache.get(_key(n, nfields, precision, var))
 
 
+def pick(results):
+    """The winning shape of a list of timed candidates (dicts with
+    "field_steps_per_s" and "threads"), tagged with the candidate count, or
+    None for an empty list.  Shapes within 1% of the fastest are a tie: the
+    one with the most threads per CTA wins (more warps to hide latency;
+    heavier per-point work such as the Kerr terms keeps more of its speed
+    there)."""
+    if not results:
+        return None
+    top = max(r["field_steps_per_s"] for r in results)
+    ties = [r for r in results if r["field_steps_per_s"] >= 0.99 * top]
+    best = max(ties, key=lambda r: (r["threads"], r["field_steps_per_s"]))
+    return dict(best, candidates=len(results))
+
+
 def tune(cfg, precision=opo.OPO_FP32_PH64, device=0, round_trips=2, candidates=None, reps=3):
     """Time every accepted launch shape for the class of ``cfg``; return the
     best as ``{"cluster", "threads", "rt_per_launch", "field_steps_per_s"}``.
@@ -125,18 +140,12 @@ def tune(cfg, precision=opo.OPO_FP32_PH64, device=0, round_trips=2, candidates=N
                     c.close()
     finally:
         probe.close()
-    if not results:
+    best = pick(results)
+    if best is None:
         return None
-    # shapes within 1% of the fastest are a tie: take the one with the most
-    # threads per CTA (more warps to hide latency; heavier per-point work
-    # such as the Kerr terms keeps more of its speed there)
-    top = max(r["field_steps_per_s"] for r in results)
-    ties = [r for r in results if r["field_steps_per_s"] >= 0.99 * top]
-    best = max(ties, key=lambda r: (r["threads"], r["field_steps_per_s"]))
-    best = dict(best, candidates=len(results))
     with _lock:
         _cache[_key(cfg.n, cfg.nfields, precision, var)] = best
     return best
 
 
-__all__ = ["tune", "lookup", "load", "save"]
+__all__ = ["tune", "pick", "variant", "lookup", "load", "save"]

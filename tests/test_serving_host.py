@@ -57,3 +57,19 @@ def test_autotune_classes_follow_the_kernel_variant():
     finally:
         with A._lock:
             A._cache.clear()
+
+
+def test_autotune_pick_prefers_larger_ctas_within_one_percent():
+    from paper_2410_02532_gb300 import autotune as A
+
+    assert A.pick([]) is None
+    r = [{"cluster": 8, "threads": 128, "field_steps_per_s": 100.0},
+         {"cluster": 4, "threads": 512, "field_steps_per_s": 99.5},
+         {"cluster": 4, "threads": 384, "field_steps_per_s": 99.8},
+         {"cluster": 16, "threads": 512, "field_steps_per_s": 90.0}]
+    best = A.pick(r)
+    assert (best["cluster"], best["threads"], best["candidates"]) == (4, 512, 4)
+    # outside the 1% band the fastest wins whatever its CTA size
+    r[1]["field_steps_per_s"] = 98.0
+    r[2]["field_steps_per_s"] = 98.9
+    assert (A.pick(r)["cluster"], A.pick(r)["threads"]) == (8, 128)
