@@ -241,8 +241,11 @@ OPO_API int opo_get_fields_device(opo_ctx *ctx, int32_t field, int32_t which, vo
  * persistent kernel per launch in which a thread-block cluster of `cluster`
  * CTAs of `threads` threads keeps the instance's fields in distributed shared
  * memory for `rt_per_launch` round trips.  0 picks the default for each of
- * cluster, rt_per_launch and threads.  OPO_E_UNSUPPORTED if the fused path
- * cannot hold the instance in that configuration. */
+ * cluster, rt_per_launch and threads; the default shapes favour batches
+ * (where two CTAs fit an SM's shared memory, CTAs small enough that the
+ * registers admit two as well), and a lone instance may run faster with
+ * larger CTAs.  OPO_E_UNSUPPORTED if the fused path cannot hold the instance
+ * in that configuration. */
 OPO_API int opo_set_path(opo_ctx *ctx, int32_t path, int32_t cluster, int32_t rt_per_launch,
                          int32_t threads);
 
@@ -267,7 +270,9 @@ OPO_API const char *opo_status_string(int status);
 
 /* Batched sweep: many instances advanced together on the fused path, one
  * thread-block cluster per instance.  Instances are grouped by (N, field
- * count); each group is one persistent launch and the groups run
+ * count, nonlinear-step kernel variant: chi(2) with a phase mismatch in some
+ * crystal, chi(2) with dk = 0 in all, or with Kerr terms, and launch shape);
+ * each group is one persistent launch and the groups run
  * concurrently.  All contexts must be on one device, in one precision, with
  * crystal and cavity set; every other parameter may differ.  The batch keeps
  * pointers to the contexts (owned by the caller; they must outlive the batch)
