@@ -162,6 +162,14 @@ typedef struct {
     int32_t cluster;          /* CTAs per instance of the fused path (0: plain)    */
 } opo_stats;
 
+/* Check a configuration without touching any GPU: the grid as opo_create
+ * checks it (apart from the device ordinal), `count` crystals as
+ * opo_set_crystals checks them (count 0: none; crystals may then be NULL)
+ * and the cavity as opo_set_cavity checks it (NULL: none).  Returns OPO_OK
+ * or OPO_E_INVALID.  The context calls run the same checks. */
+OPO_API int opo_validate(const opo_grid *grid, const opo_crystal *crystals, int32_t count,
+                         const opo_cavity *cavity);
+
 /* Create a context for one OPO instance on grid->device.  Fields start at
  * zero; a zero signal never grows, so seed it with opo_set_fields.
  * Returns OPO_E_INVALID for a bad grid, OPO_E_CUDA if the device is missing,
@@ -329,8 +337,10 @@ OPO_API int opo_batch_get_trace(opo_batch *batch, double *host, int64_t rows);
  *         work overlaps on the GPU (other streams, other threads) race on the
  *         shared scratch: serialize them.
  * Set-up: the first call on a device looks up the array's device address with
- *         that device current (no allocation); make that first call before any
- *         stream capture. */
+ *         that device current (no allocation) and keeps it for later calls;
+ *         make that first call before any stream capture.  A device reset
+ *         (cudaDeviceReset) in the process invalidates the kept address: do
+ *         not call this entry point on that device after one. */
 OPO_API int opo_crystal_pass_noalloc(const opo_grid *grid, const opo_crystal *crystal,
                                      void *fields, void *stream);
 

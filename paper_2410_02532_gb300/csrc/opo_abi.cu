@@ -308,52 +308,6 @@ int build_graph(opo_ctx *c)
     return OPO_OK;
 }
 
-// Validate the ranges shared by crystal and cavity checks.
-bool valid_crystal(const opo_ctx *c, const opo_crystal *k)
-{
-    if (!(k->length_m > 0.0) || !std::isfinite(k->length_m) || k->nz < 1 || k->nz > 1000000)
-        return false;
-    if (!std::isfinite(k->dk_per_m) || !std::isfinite(k->deff_mpv) || !(k->w0_m > 0.0) ||
-        !std::isfinite(k->w0_m) || !std::isfinite(k->tod_div) || k->tod_div < 0.0)
-        return false;
-    if (!finite_all(k->lambda_m, 3) || !finite_all(k->n, 3) || !finite_all(k->alpha_per_m, 3) ||
-        !finite_all(k->dbeta1_s_per_m, 3) || !finite_all(k->beta2_s2_per_m, 3) ||
-        !finite_all(k->beta3_s3_per_m, 3) || !finite_all(k->beta4_s4_per_m, 3) ||
-        !std::isfinite(k->n2_m2_per_W))
-        return false;
-    for (int x = 0; x < c->F; x++)
-        if (!(k->lambda_m[x] > 0.0) || !(k->n[x] > 0.0))
-            return false;
-    return true;
-}
-
-bool valid_cavity(const opo_ctx *c, const opo_cavity *v)
-{
-    if (v->resonant_mask >> c->F)
-        return false;
-    for (int x = 0; x < 3; x++)
-        if (!(v->R[x] >= 0.0 && v->R[x] <= 1.0))
-            return false;
-    if (!finite_all(v->delta_rad, 3) || !finite_all(v->gdd_s2, 3) || !std::isfinite(v->delay_s) ||
-        !std::isfinite(v->eom_beta_rad) || !std::isfinite(v->eom_f_hz) ||
-        !std::isfinite(v->t_rt_s) || v->t_rt_s < 0.0 || !std::isfinite(v->pump_power_W) ||
-        v->pump_power_W < 0.0 || !std::isfinite(v->pump_fwhm_s))
-        return false;
-    if (v->pump_kind < OPO_PUMP_CW || v->pump_kind > OPO_PUMP_NS)
-        return false;
-    if (!std::isfinite(v->pump_t0_s))
-        return OPO_E_INVALID;
-    if ((v->pump_kind == OPO_PUMP_SECH2 || v->pump_kind == OPO_PUMP_NS) && !(v->pump_fwhm_s > 0.0))
-        return false;
-    if (v->pump_kind == OPO_PUMP_USER) {
-        if (!v->pump_user)
-            return false;
-        if (!finite_all(v->pump_user, 2 * c->n))
-            return false;
-    }
-    return true;
-}
-
 int choose_path(opo_ctx *c, FusedCfg *cfg)
 {
     if (c->path_req == OPO_PATH_PLAIN)
@@ -378,7 +332,103 @@ int begin_call(opo_ctx *c, int64_t M, int parts, bool plain)
 
 } // namespace
 
+namespace opo {
+
+// The grid checks of opo_create that need no device: N a power of two in
+// [16, 2^17], a finite positive window, two or three fields, a known
+// precision.
+bool valid_grid_shape(const opo_grid *g)
+{
+    if (!is_pow2(g->n) || g->n < 16 || g->n > (1 << 17))
+        return false;
+    if (!(g->t_window_s > 0.0) || !std::isfinite(g->t_window_s))
+        return false;
+    if (g->nfields != 2 && g->nfields != 3)
+        return false;
+    return g->precision == OPO_FP64 || g->precision == OPO_FP32_PH64;
+}
+
+// A crystal for F fields: positive finite length, 1..10^6 steps, finite
+// parameters, positive wavelengths and indices of the used fields, waist > 0,
+// TOD divisor finite and >= 0 (0 selects 6).
+bool valid_crystal_for(int F, const opo_crystal *k)
+{
+    if (!(k->length_m > 0.0) || !std::isfinite(k->length_m) || k->nz < 1 || k->nz > 1000000)
+        return false;
+    if (!std::isfinite(k->dk_per_m) || !std::isfinite(k->deff_mpv) || !(k->w0_m > 0.0) ||
+        !std::isfinite(k->w0_m) || !std::isfinite(k->tod_div) || k->tod_div < 0.0)
+        return false;
+    if (!finite_all(k->lambda_m, 3) || !finite_all(k->n, 3) || !finite_all(k->alpha_per_m, 3) ||
+        !finite_all(k->dbeta1_s_per_m, 3) || !finite_all(k->beta2_s2_per_m, 3) ||
+        !finite_all(k->beta3_s3_per_m, 3) || !finite_all(k->beta4_s4_per_m, 3) ||
+        !std::isfinite(k->n2_m2_per_W))
+        return false;
+    for (int x = 0; x < F; x++)
+        if (!(k->lambda_m[x] > 0.0) || !(k->n[x] > 0.0))
+            return false;
+    return true;
+}
+
+// A cavity for F fields of N points: resonant bits only for existing fields,
+// 0 <= R <= 1, finite phases, GDD, delay, EOM and pump parameters, a known
+// pump kind with a positive width where it needs one and a finite user
+// profile where it is used.
+bool valid_cavity_for(int F, int n, const opo_cavity *v)
+{
+    if (v->resonant_mask >> F)
+        return false;
+    for (int x = 0; x < 3; x++)
+        if (!(v->R[x] >= 0.0 && v->R[x] <= 1.0))
+            return false;
+    if (!finite_all(v->delta_rad, 3) || !finite_all(v->gdd_s2, 3) || !std::isfinite(v->delay_s) ||
+        !std::isfinite(v->eom_beta_rad) || !std::isfinite(v->eom_f_hz) ||
+        !std::isfinite(v->t_rt_s) || v->t_rt_s < 0.0 || !std::isfinite(v->pump_power_W) ||
+        v->pump_power_W < 0.0 || !std::isfinite(v->pump_fwhm_s) || !std::isfinite(v->pump_t0_s))
+        return false;
+    if (v->pump_kind < OPO_PUMP_CW || v->pump_kind > OPO_PUMP_NS)
+        return false;
+    if ((v->pump_kind == OPO_PUMP_SECH2 || v->pump_kind == OPO_PUMP_NS) && !(v->pump_fwhm_s > 0.0))
+        return false;
+    if (v->pump_kind == OPO_PUMP_USER) {
+        if (!v->pump_user)
+            return false;
+        if (!finite_all(v->pump_user, 2 * n))
+            return false;
+    }
+    return true;
+}
+
+// Crystals of one round trip: each valid for F fields, the same wavelengths
+// in all of them.
+bool valid_crystals_for(int F, const opo_crystal *list, int count)
+{
+    if (!list || count < 1 || count > OPO_MAX_CRYSTALS)
+        return false;
+    for (int i = 0; i < count; i++) {
+        if (!valid_crystal_for(F, &list[i]))
+            return false;
+        for (int x = 0; x < F; x++)
+            if (list[i].lambda_m[x] != list[0].lambda_m[x])
+                return false; // the same fields in every crystal
+    }
+    return true;
+}
+
+} // namespace opo
+
 extern "C" {
+
+int opo_validate(const opo_grid *grid, const opo_crystal *crystals, int32_t count,
+                 const opo_cavity *cavity)
+{
+    if (!grid || !valid_grid_shape(grid) || count < 0)
+        return OPO_E_INVALID;
+    if (count > 0 && !valid_crystals_for(grid->nfields, crystals, count))
+        return OPO_E_INVALID;
+    if (cavity && !valid_cavity_for(grid->nfields, grid->n, cavity))
+        return OPO_E_INVALID;
+    return OPO_OK;
+}
 
 const char *opo_status_string(int s)
 {
@@ -402,13 +452,7 @@ int opo_create(opo_ctx **out, const opo_grid *grid)
     *out = nullptr;
     if (!grid)
         return OPO_E_INVALID;
-    if (!is_pow2(grid->n) || grid->n < 16 || grid->n > (1 << 17))
-        return OPO_E_INVALID;
-    if (!(grid->t_window_s > 0.0) || !std::isfinite(grid->t_window_s))
-        return OPO_E_INVALID;
-    if (grid->nfields != 2 && grid->nfields != 3)
-        return OPO_E_INVALID;
-    if (grid->precision != OPO_FP64 && grid->precision != OPO_FP32_PH64)
+    if (!valid_grid_shape(grid))
         return OPO_E_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -512,15 +556,8 @@ static int ensure_buf(opo_ctx *c, void **p, int *cap, int want, size_t elem)
 
 int opo_set_crystals(opo_ctx *c, const opo_crystal *list, int32_t count)
 {
-    if (!c || !list || count < 1 || count > OPO_MAX_CRYSTALS)
+    if (!c || !valid_crystals_for(c->F, list, count))
         return OPO_E_INVALID;
-    for (int i = 0; i < count; i++) {
-        if (!valid_crystal(c, &list[i]))
-            return OPO_E_INVALID;
-        for (int x = 0; x < c->F; x++)
-            if (list[i].lambda_m[x] != list[0].lambda_m[x])
-                return OPO_E_INVALID; // the same fields in every crystal
-    }
     DeviceGuard g(c->device);
     if (!g.ok)
         return OPO_E_CUDA;
@@ -563,7 +600,7 @@ int opo_set_cavity(opo_ctx *c, const opo_cavity *v)
 {
     if (!c || !v)
         return OPO_E_INVALID;
-    if (!valid_cavity(c, v))
+    if (!valid_cavity_for(c->F, c->n, v))
         return OPO_E_INVALID;
     DeviceGuard g(c->device);
     if (!g.ok)

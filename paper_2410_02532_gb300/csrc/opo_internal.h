@@ -132,6 +132,13 @@ struct opo_ctx {
 
 namespace opo {
 
+// opo_abi.cu: argument checks shared by the context calls, opo_validate
+// and the allocation-free pass (no device access)
+bool valid_grid_shape(const opo_grid *g);
+bool valid_crystal_for(int F, const opo_crystal *k);
+bool valid_crystals_for(int F, const opo_crystal *list, int count);
+bool valid_cavity_for(int F, int n, const opo_cavity *v);
+
 // opo_setup.cu
 int setup_twiddles(opo_ctx *c);
 // tables of every crystal and the device copy of their descriptors

@@ -48,27 +48,11 @@ extern "C" OPO_API int opo_crystal_pass_noalloc(const opo_grid *grid, const opo_
 {
     if (!grid || !k || !fields)
         return OPO_E_INVALID;
+    // the checks of opo_create and opo_set_crystal
+    if (!opo::valid_grid_shape(grid) || !opo::valid_crystal_for(grid->nfields, k))
+        return OPO_E_INVALID;
     const int n = grid->n;
-    if (n < 16 || n > (1 << 17) || (n & (n - 1)) != 0)
-        return OPO_E_INVALID;
-    if (grid->nfields != 2 && grid->nfields != 3)
-        return OPO_E_INVALID;
-    if (grid->precision != OPO_FP64 && grid->precision != OPO_FP32_PH64)
-        return OPO_E_INVALID;
-    if (!(grid->t_window_s > 0.0) || !std::isfinite(grid->t_window_s))
-        return OPO_E_INVALID;
-    if (!(k->length_m > 0.0) || !std::isfinite(k->length_m) || k->nz < 1 || k->nz > 100000 ||
-        !std::isfinite(k->dk_per_m) || !std::isfinite(k->deff_mpv))
-        return OPO_E_INVALID;
     const int F = grid->nfields;
-    for (int x = 0; x < F; x++)
-        if (!(k->lambda_m[x] > 0.0) || !(k->n[x] > 0.0) || !std::isfinite(k->lambda_m[x]) ||
-            !std::isfinite(k->n[x]) || !std::isfinite(k->alpha_per_m[x]) ||
-            !std::isfinite(k->dbeta1_s_per_m[x]) || !std::isfinite(k->beta2_s2_per_m[x]) ||
-            !std::isfinite(k->beta3_s3_per_m[x]) || !std::isfinite(k->beta4_s4_per_m[x]))
-            return OPO_E_INVALID;
-    if (!std::isfinite(k->n2_m2_per_W))
-        return OPO_E_INVALID;
     const bool dbl = grid->precision == OPO_FP64;
     const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
     // scratch layout: twiddles N | FFT intermediate F*N | dispersion F*N | ekz 4 nz + 1

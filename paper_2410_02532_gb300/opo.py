@@ -69,6 +69,8 @@ _P = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
 
 _SIGS = {
+    "opo_validate": ([ctypes.POINTER(Grid), ctypes.POINTER(Crystal), ctypes.c_int32,
+                      ctypes.POINTER(Cavity)], ctypes.c_int),
     "opo_create": ([ctypes.POINTER(_P), ctypes.POINTER(Grid)], ctypes.c_int),
     "opo_set_crystal": ([_P, ctypes.POINTER(Crystal)], ctypes.c_int),
     "opo_set_crystals": ([_P, ctypes.POINTER(Crystal), ctypes.c_int32], ctypes.c_int),
@@ -138,6 +140,14 @@ def _cplx_in(a, n):
 
 
 # ---- thin wrappers with the C names ----------------------------------------
+
+def opo_validate(grid: Grid, crystals=(), cavity=None) -> int:
+    """Status of the configuration's checks (no GPU involved): OPO_OK or
+    OPO_E_INVALID."""
+    arr = (Crystal * len(crystals))(*crystals) if crystals else None
+    return lib().opo_validate(ctypes.byref(grid), arr, len(crystals),
+                              ctypes.byref(cavity) if cavity is not None else None)
+
 
 def opo_create(grid: Grid):
     h = _P()

@@ -7,6 +7,7 @@ per field): FP64 path <= 1e-10, FP32 fields with FP64 phases <= 1e-4.
 import numpy as np
 import pytest
 
+import parity_log
 from oracle import oracle as orc
 from paper_2410_02532_gb300 import opo
 from paper_2410_02532_gb300 import workloads as W
@@ -51,18 +52,26 @@ def spectral_width(cfg, a):
     return float(np.sqrt(np.sum((f - mu) ** 2 * X) / np.sum(X)))
 
 
-def compare(cfg, got, ref, prec, what=""):
+def compare(cfg, got, ref, prec, what="", test="parity"):
+    """Element-by-element comparison of one GPU result (fields, output
+    fields, trace, stats) with the oracle's; records the measured errors."""
     tol = TOL[prec]
     g_f, g_o, g_t = got[:3]
     r_f, r_o, r_t = ref
+    ef = [rel_l2(g_f[x], r_f[x]) for x in range(cfg.nfields)]
+    eo = [rel_l2(g_o[x], r_o[x]) for x in range(cfg.nfields)]
+    ep = [abs(g_t[-1, x] - r_t[-1, x]) / max(abs(r_t[-1, x]), 1e-300) for x in range(cfg.nfields)]
+    w = max(spectral_width(cfg, r_o[1]), 0.5 / cfg.t_window)
+    ec = abs(g_t[-1, 3] - r_t[-1, 3]) / w
+    path = got[3].path if len(got) > 3 and got[3] is not None else -1
+    parity_log.record(test, what, prec, path, n=cfg.n, fields=cfg.nfields, nz=cfg.nz,
+                      rel_l2_fields=max(ef), rel_l2_outputs=max(eo), rel_power=max(ep),
+                      centroid_over_width=ec, tol=tol)
     for x in range(cfg.nfields):
-        e = rel_l2(g_f[x], r_f[x])
-        assert e <= tol, (what, "field", x, e)
-        e = rel_l2(g_o[x], r_o[x])
-        assert e <= tol, (what, "output", x, e)
+        assert ef[x] <= tol, (what, "field", x, ef[x])
+        assert eo[x] <= tol, (what, "output", x, eo[x])
     for x in range(cfg.nfields):
         assert abs(g_t[-1, x] - r_t[-1, x]) <= 4 * tol * abs(r_t[-1, x]) + 1e-300, (what, "P", x)
-    w = max(spectral_width(cfg, r_o[1]), 0.5 / cfg.t_window)
     assert abs(g_t[-1, 3] - r_t[-1, 3]) <= 4 * tol * w, (what, "centroid")
 
 
@@ -298,9 +307,12 @@ def test_specialised_fused_round_trip(case, prec):
     ref = oracle_rt(cfg, a0, m0=5)
     try:
         got = gpu_rt(cfg, a0, prec, opo.OPO_PATH_FUSED, m0=5)
-    except opo.OPOError as e:  # FP64 at 2^15 does not fit a cluster
-        assert e.status == opo.OPO_E_UNSUPPORTED and prec == opo.OPO_FP64
-        return
+    except opo.OPOError as e:
+        # a size the fused kernels cannot hold in this precision: the path
+        # that runs for it (automatic choice) is compared instead
+        assert e.status == opo.OPO_E_UNSUPPORTED
+        got = gpu_rt(cfg, a0, prec, opo.OPO_PATH_AUTO, m0=5)
+        assert got[3].path == opo.OPO_PATH_PLAIN
     compare(cfg, got, ref, prec, case)
 
 
@@ -511,3 +523,41 @@ def test_batch_host_transfers_match_per_context_calls():
     finally:
         for c in ctxs:
             c.close()
+
+
+# ------------- the plain path at full size, and the sizes the automatic
+# choice sends to it (one round trip from the same stored state, element by
+# element against the oracle)
+
+LARGE_CASES = [
+    ("plain_n16384_gdd", lambda: W.cw_sro_16k().replace(nz=4), opo.OPO_FP32_PH64,
+     opo.OPO_PATH_PLAIN),
+    ("plain_n16384_gdd", lambda: W.cw_sro_16k().replace(nz=4), opo.OPO_FP64, opo.OPO_PATH_PLAIN),
+    ("auto_n32768_gdd", lambda: W.cw_sro_16k().replace(n=1 << 15, nz=3), opo.OPO_FP64,
+     opo.OPO_PATH_AUTO),
+    ("auto_n65536_sync_eom", lambda: W.sync_pumped_64k(delay_fs=-10.0).replace(nz=3),
+     opo.OPO_FP64, opo.OPO_PATH_AUTO),
+    ("auto_n131072_sync_eom", lambda: W.sync_pumped_64k(delay_fs=20.0).replace(n=1 << 17, nz=3),
+     opo.OPO_FP32_PH64, opo.OPO_PATH_AUTO),
+    ("auto_n131072_sync_eom", lambda: W.sync_pumped_64k(delay_fs=20.0).replace(n=1 << 17, nz=2),
+     opo.OPO_FP64, opo.OPO_PATH_AUTO),
+    ("plain_n131072_degenerate_dk", lambda: cfg_degenerate(n=1 << 17).replace(nz=3),
+     opo.OPO_FP32_PH64, opo.OPO_PATH_PLAIN),
+    ("plain_n65536_dro_loss_dk", lambda: cfg_dro(n=1 << 16).replace(nz=3), opo.OPO_FP32_PH64,
+     opo.OPO_PATH_PLAIN),
+]
+
+
+@pytest.mark.parametrize("name,make,prec,path", LARGE_CASES,
+                         ids=["%s-%s" % (c[0], "fp64" if c[2] == opo.OPO_FP64 else "fp32ph64")
+                              for c in LARGE_CASES])
+def test_large_n_round_trip(name, make, prec, path):
+    """The plain per-operation chain at 2^14..2^17 and every size/precision
+    that the automatic path choice runs, against the oracle per pass."""
+    cfg = make()
+    a0 = strong(cfg, 1e6)
+    ref = oracle_rt(cfg, a0, m0=3)
+    got = gpu_rt(cfg, a0, prec, path, m0=3)
+    compare(cfg, got, ref, prec, name, test="large_n")
+    if path != opo.OPO_PATH_AUTO:
+        assert got[3].path == path

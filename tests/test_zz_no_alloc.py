@@ -7,9 +7,10 @@ scratch in a fixed device array inside the library.  Here it is checked,
 through the C ABI and on two calls in a row, against the context API: a
 plain-path round trip whose cavity is transparent (every field resonant,
 R = 1, no detuning, GDD, delay or EOM, no input pump) is exactly one crystal
-pass.  This file
-sorts last so that a run stopping at the first failure has run everything
-else first.
+pass of the same kernels with the same tables, so the two agree bit for bit.
+One case sits at the largest size the fixed scratch accepts (three FP32
+fields of 2^16 points); the next size up is refused.  This file sorts last so
+that a run stopping at the first failure has run everything else first.
 """
 import ctypes
 
@@ -21,8 +22,6 @@ from paper_2410_02532_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {opo.OPO_FP64: 1e-10, opo.OPO_FP32_PH64: 1e-4}
-
 
 def _lib():
     from paper_2410_02532_gb300 import build
@@ -32,10 +31,6 @@ def _lib():
                                            ctypes.c_void_p, ctypes.c_void_p]
     L.opo_crystal_pass_noalloc.restype = ctypes.c_int
     return L
-
-
-def _rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def _transparent(cfg):
@@ -63,17 +58,23 @@ def _start(cfg):
 
 
 CASES = {
-    "3field_dispersive_dk": W.cw_sro_16k().replace(n=1024, nz=12, dk=120.0),
-    "2field_degenerate": W.degenerate_2field(n=2048, level=3.0).replace(nz=9, dk=-40.0),
+    "3field_dispersive_dk": (W.cw_sro_16k().replace(n=1024, nz=12, dk=120.0), None),
+    "2field_degenerate": (W.degenerate_2field(n=2048, level=3.0).replace(nz=9, dk=-40.0), None),
+    # the largest accepted size: 3 x 2^16 FP32 fields (3.5 MiB of the 4 MiB scratch)
+    "3field_n65536_largest": (W.sync_pumped_64k(delay_fs=10.0).replace(nz=3),
+                              opo.OPO_FP32_PH64),
 }
+PARAMS = [(c, p) for c in sorted(CASES) for p in (opo.OPO_FP64, opo.OPO_FP32_PH64)
+          if CASES[c][1] in (None, p)]
 
 
-@pytest.mark.parametrize("prec", [opo.OPO_FP64, opo.OPO_FP32_PH64], ids=["fp64", "fp32ph64"])
-@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("case,prec", PARAMS,
+                         ids=["%s-%s" % (c, "fp64" if p == opo.OPO_FP64 else "fp32ph64")
+                              for c, p in PARAMS])
 def test_noalloc_pass_matches_context_api(case, prec):
     torch = pytest.importorskip("torch")
     L = _lib()
-    cfg = CASES[case]
+    cfg = CASES[case][0]
     a0 = _start(cfg)
     ref = _context_passes(cfg, a0, prec, 2)
     dt = torch.complex128 if prec == opo.OPO_FP64 else torch.complex64
@@ -87,8 +88,8 @@ def test_noalloc_pass_matches_context_api(case, prec):
         assert st == opo.OPO_OK, opo.status_string(st)
         torch.cuda.synchronize()
         got = dev.cpu().numpy().astype(np.complex128)
-        for x in range(cfg.nfields):
-            assert _rel_l2(got[x], ref[call][x]) <= TOL[prec], (case, call, x)
+        # the same kernels, tables and arguments: bit for bit
+        assert np.array_equal(got, ref[call]), (case, call)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -102,3 +103,16 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert st == opo.OPO_E_INVALID
     assert L.opo_crystal_pass_noalloc(None, ctypes.byref(crys), buf.data_ptr(), None) == \
         opo.OPO_E_INVALID
+    # one size above the largest accepted FP32 request: 3 x 2^17 points (7 MiB)
+    big = cfg.replace(n=1 << 17)
+    st = L.opo_crystal_pass_noalloc(ctypes.byref(opo.grid_from(big, opo.OPO_FP32_PH64)),
+                                    ctypes.byref(opo.crystal_from(big)), buf.data_ptr(), None)
+    assert st == opo.OPO_E_INVALID
+    # the crystal checks of opo_set_crystal apply here too (a negative TOD
+    # divisor is refused by both)
+    small = W.cw_sro_1024()
+    bad = opo.crystal_from(small)
+    bad.tod_div = -6.0
+    st = L.opo_crystal_pass_noalloc(ctypes.byref(opo.grid_from(small)), ctypes.byref(bad),
+                                    buf.data_ptr(), None)
+    assert st == opo.OPO_E_INVALID
