@@ -61,6 +61,9 @@ def parse():
                     help="only the headline number (no plain/e2e/cpu legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true", help="default launch shape, no autotuning")
+    ap.add_argument("--serving-full", type=int, default=0, metavar="COUNT",
+                    help="also serve the request stream at its stated budgets (100-5000 round "
+                         "trips): the 200/s trace for 90 s and COUNT requests at 0.7 capacity")
     return ap.parse_args()
 
 
@@ -304,9 +307,19 @@ def main():
         # CTA sizes
         extras = single_and_plain(args, opo, W, base, prec, local, torch)
         extras["e2e"] = e2e(args, opo, W, ctxs, batch, base, torch, np)
+        pb = plain_batched_leg(opo, W, prec, local, torch, base, (B, 8 * B))
+        extras["plain_batched"] = pb
+        if "ms_per_round_trip" in pb.get("B%d" % B, {}):
+            extras["fused_over_plain_batched"] = (pb["B%d" % B]["ms_per_round_trip"]
+                                                  / statistics.median(step_ms))
         extras["batched_sweep"] = sweep_leg(opo, W, prec, local, torch)
         extras["variants_2e14"] = rows_leg(opo, W, prec, local, torch, base, cluster, th_req)
         extras["serving"] = serving_leg(prec, local, value, base)
+        if args.serving_full:
+            extras["serving_full_budgets"] = serving_full_leg(
+                prec, local, extras["serving"].pop("capacity"), args.serving_full)
+        else:
+            extras["serving"].pop("capacity", None)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -339,6 +352,76 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def plain_bytes_per_roundtrip(cfg, csz):
+    """Algorithmic HBM bytes of one plain-path round trip of one instance:
+    per z-step and point-field, RK4 half steps 2 x (read + write), forward and
+    inverse FFT 2 x (column pass + row pass) x (read + write), dispersion
+    factor read + write + table read: 15 csz; per round trip the entry, the
+    power sums, the output copy, the cavity visit (FFT pair, factor) and the
+    mirror/EOM pass, about 16 csz per point-field."""
+    n, F = cfg.n, cfg.nfields
+    return n * F * csz * (15 * total_nz(cfg) + 16)
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def plain_batched_leg(opo, W, prec, local, torch, base, counts, steps=6):
+    """The plain per-operation chain on batches of the headline workload: every
+    launch applies one operation to all instances (one graph per round trip).
+    Timed like the headline (one round trip per step, L2 flushed between
+    steps, CUDA events on the launch stream, median step).  ``counts``: batch
+    sizes; the first equals the fused headline batch, a larger one has a
+    working set beyond L2, where the chain is bound by HBM bandwidth."""
+    csz = 16 if prec == opo.OPO_FP64 else 8
+    peak, peak_src = measured_hbm_gbs()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for B in counts:
+        s = torch.cuda.Stream()
+        ctxs = []
+        try:
+            for i in range(B):
+                c = opo.Context(base.replace(instance=900000 + i), precision=prec, device=local,
+                                stream=s.cuda_stream)
+                c.set_path(opo.OPO_PATH_PLAIN)
+                ctxs.append(c)
+            b = opo.opo_batch_create([c.h for c in ctxs], 0, 0)
+            times = []
+            with torch.cuda.stream(s):
+                for _ in range(2):
+                    opo.opo_batch_run(b, 1)
+                for _ in range(steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    opo.opo_batch_run(b, 1)
+                    e1.record(s)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+            opo.opo_batch_destroy(b)
+            ms = statistics.median(times)
+            gbs = plain_bytes_per_roundtrip(base, csz) * B / (ms * 1e-3) / 1e9
+            out["B%d" % B] = {
+                "instances": B, "ms_per_round_trip": ms,
+                "field_steps_per_s": B * base.nfields * total_nz(base) / (ms * 1e-3),
+                "working_set_MB": B * base.n * base.nfields * csz * 3 / 1e6,
+                "algorithmic_GB_per_s": gbs, "hbm_peak_GB_per_s": peak,
+                "hbm_peak": peak_src, "frac_hbm": gbs / peak}
+        except opo.OPOError as e:
+            out["B%d" % B] = {"error": str(e)}
+        finally:
+            for c in ctxs:
+                c.close()
+    return out
 
 
 def single_and_plain(args, opo, W, base, prec, local, torch, cl_req=0):
@@ -552,7 +635,60 @@ def serving_leg(prec, local, batch_value, base, count=1000):
                "note": "rate = 0.7 x the server's saturated throughput on the same request mix; "
                        "200 requests/s with 100-5000 round trips would offer about %.0fx that "
                        "capacity" % full_load})
+    # the same trace with every request on the batched plain path (same
+    # admission shares): the plain chain's latency on the same stream
+    srv = serving.Server(precision=prec, device=local, tick_rt=16, path="plain")
+    t0 = time.perf_counter()
+    res_p = srv.run(reqs, max_wall_s=3 * wall)
+    wall_p = time.perf_counter() - t0
+    stp = serving.latency_stats(res_p)
+    done_p = {x.rid for x in res_p}
+    stp.update({"completed": len(res_p), "wall_s": wall_p,
+                "point_field_steps_per_s": sum(serving.request_work(r) for r in reqs
+                                               if r.rid in done_p) / wall_p,
+                "note": "same requests and arrival times on the batched plain path; requests "
+                        "not finished within 3x the fused run's wall time are left out"})
+    st["plain_path"] = stp
+    if stp.get("p99_s") and len(res_p) == len(res):
+        st["p99_plain_over_fused"] = stp["p99_s"] / st["p99_s"]
+    st["capacity"] = cap
     return st
+
+
+def serving_full_leg(prec, local, cap, count, window_s=90.0):
+    """Config-5 request stream at its stated budgets (N = 2^12..2^17, 100..5000
+    round trips, 2 or 3 fields, CW or pulsed).  (1) The first 2000 arrivals at
+    200 requests/s, served for ``window_s`` seconds: the offered load is
+    hundreds of times the capacity, so the report is how many finished and
+    their latencies, with the rest still queued.  (2) ``count`` arrivals at
+    0.7 of the capacity measured on the short-budget mix: p50/p99."""
+    from paper_2410_02532_gb300 import serving
+    exps = (12, 13, 14, 15, 16, 17)
+    rounds = (100, 5000)
+    out = {}
+    reqs = serving.poisson_trace(2000, 200.0, seed=20241011, n_exps=exps, rounds=rounds)
+    mean_work = sum(serving.request_work(r) for r in reqs) / len(reqs)
+    srv = serving.Server(precision=prec, device=local, tick_rt=32)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, max_wall_s=window_s)
+    wall = time.perf_counter() - t0
+    st = serving.latency_stats(res)
+    st.update({"arrivals": len(reqs), "rate_hz": 200.0, "completed": len(res),
+               "window_s": wall, "offered_over_capacity": 200.0 * mean_work / cap,
+               "field_steps_per_s": srv.field_steps / wall,
+               "note": "latencies of the requests finished inside the window only"})
+    out["rate_200_per_s"] = st
+    rate = 0.7 * cap / mean_work
+    reqs = serving.poisson_trace(count, rate, seed=20241012, n_exps=exps, rounds=rounds)
+    srv = serving.Server(precision=prec, device=local, tick_rt=32)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, max_wall_s=6 * count / rate)
+    wall = time.perf_counter() - t0
+    st = serving.latency_stats(res)
+    st.update({"requests": count, "completed": len(res), "rate_hz": rate, "offered_load": 0.7,
+               "wall_s": wall, "field_steps_per_s": srv.field_steps / wall})
+    out["rate_0p7_capacity"] = st
+    return out
 
 
 if __name__ == "__main__":

@@ -276,23 +276,32 @@ OPO_API int opo_destroy(opo_ctx *ctx);
 /* Static string for a status code. */
 OPO_API const char *opo_status_string(int status);
 
-/* Batched sweep: many instances advanced together on the fused path, one
- * thread-block cluster per instance.  Instances are grouped by (N, field
+/* Batched sweep: many instances advanced together.  A member whose
+ * opo_set_path asks for the fused path, or leaves the choice to the library
+ * (OPO_PATH_AUTO) at a size the fused kernels hold, runs on the fused path,
+ * one thread-block cluster per instance; these are grouped by (N, field
  * count, nonlinear-step kernel variant: chi(2) with a phase mismatch in some
- * crystal, chi(2) with dk = 0 in all, or with Kerr terms, and launch shape);
- * each group is one persistent launch and the groups run
- * concurrently.  All contexts must be on one device, in one precision, with
+ * crystal, chi(2) with dk = 0 in all, or with Kerr terms, and launch shape),
+ * each group one persistent launch.  The other members run on the plain path
+ * (one kernel per operation, Sec. 2.2 and the main loop of Sec. 4.1), grouped
+ * by (N, field count, the crystals' step counts): every launch of a group
+ * applies one operation to all of its members, and one round trip of the
+ * group is a captured graph.  The groups run concurrently.  A member whose
+ * crystals or path request change after opo_batch_create so that it no
+ * longer fits its group makes opo_batch_run return OPO_E_STATE (make a new
+ * batch).  All contexts must be on one device, in one precision, with
  * crystal and cavity set; every other parameter may differ.  The batch keeps
  * pointers to the contexts (owned by the caller; they must outlive the batch)
  * and is ordered on the first context's stream.  opo_batch_run needs every
  * member alive; opo_batch_destroy does not read the members (it waits for the
  * device), so a batch may be destroyed after or before its contexts.  Each instance advances
- * bit-for-bit as opo_run_roundtrips would advance it alone on the fused path
+ * bit-for-bit as opo_run_roundtrips would advance it alone on the same path
  * with the same launch shape: `cluster` and `threads` apply to every
  * instance when nonzero; where zero, each instance keeps the cluster size,
  * CTA size and round trips per launch of its own opo_set_path (default 0:
  * the library's choice for its size class).
- * OPO_E_UNSUPPORTED if some group cannot run with that cluster size. */
+ * OPO_E_UNSUPPORTED if a member that asks for the fused path cannot run with
+ * that cluster size. */
 OPO_API int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster,
                              int32_t threads);
 OPO_API int opo_batch_run(opo_batch *batch, int64_t m);

@@ -160,7 +160,7 @@ int blocks(int64_t work)
 
 void free_all(opo_ctx *c)
 {
-    void *bufs[] = {c->d_fields, c->d_out, c->d_scratch, c->d_pump, c->d_disp, c->d_gdd,
+    void *bufs[] = {c->d_fields, c->d_out, c->d_scratch, c->d_xg, c->d_pump, c->d_disp, c->d_gdd,
                     c->d_disp_t, c->d_gdd_t,
                     c->d_tw, c->d_ekz, c->d_pump_user, c->d_obs, c->d_trace, c->d_ctl,
                     c->d_stage};
@@ -486,6 +486,10 @@ int opo_create(opo_ctx **out, const opo_grid *grid)
     alloc(&c->d_fields, fb);
     alloc(&c->d_out, fb);
     alloc(&c->d_scratch, fb);
+    // the sizes whose fused form exchanges through global memory need a
+    // second exchange buffer
+    if ((c->prec == OPO_FP32_PH64 && c->n == (1 << 17)) || (c->prec == OPO_FP64 && c->n == (1 << 16)))
+        alloc(&c->d_xg, fb);
     alloc(&c->d_disp, fb);
     alloc(&c->d_gdd, fb);
     alloc(&c->d_disp_t, fb);
@@ -582,6 +586,7 @@ int opo_set_crystals(opo_ctx *c, const opo_crystal *list, int32_t count)
     c->ncry = count;
     c->have_crystal = true;
     c->graph_valid = false;
+    c->gen++;
     derive(c);
     rc = setup_crystal_tables(c);
     if (rc == OPO_OK && c->have_cavity)
@@ -614,6 +619,7 @@ int opo_set_cavity(opo_ctx *c, const opo_cavity *v)
     }
     c->have_cavity = true;
     c->graph_valid = false;
+    c->gen++;
     if (c->have_crystal) {
         derive(c);
         return setup_cavity_tables(c);
@@ -746,6 +752,7 @@ int opo_set_output_history(opo_ctx *c, int64_t max_rt)
     c->d_hist = nullptr;
     c->hist_cap = 0;
     c->graph_valid = false;
+    c->gen++;
     if (max_rt == 0)
         return OPO_OK;
     if (cudaMalloc(&c->d_hist, row * (size_t)max_rt) != cudaSuccess) {
@@ -890,13 +897,22 @@ int opo_sync(opo_ctx *c)
 
 } // extern "C"
 
-// A batch is split into groups of equal (N, field count); each group runs
-// as one fused launch with the configuration a lone instance of that group
-// would get for the requested cluster size, so every instance advances
+// A batch is split into groups.  A fused group holds instances of equal
+// (N, field count, nonlinear-step variant, launch shape) and runs as one
+// fused launch with the configuration a lone instance of that group would
+// get; a plain group holds instances of equal (N, field count, crystals'
+// step counts) on the plain path and runs one launch per operation for all of
+// them (a captured graph per round trip).  Either way every instance advances
 // bit-for-bit as it would alone.  Groups run concurrently on forked streams.
 struct BatchGroup {
     std::vector<opo_ctx *> ctxs;
     FusedCfg cfg{};
+    bool plain = false;
+    std::vector<int> nzs;              // plain: every crystal's step count
+    opo::PlainInst *d_insts = nullptr; // plain: member descriptors (device)
+    opo::PlainCall *d_calls = nullptr; // plain: per-call values (device)
+    std::vector<opo::PlainInst> h_insts;
+    cudaGraphExec_t graph = nullptr;   // plain: one round trip of every member
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
 };
@@ -904,6 +920,7 @@ struct BatchGroup {
 struct opo_batch {
     std::vector<opo_ctx *> ctxs;
     std::vector<BatchGroup> groups;
+    cudaStream_t capture = nullptr; // capture of the plain groups' graphs
     std::vector<cudaEvent_t> ev; // one per context: stream ordering
     cudaEvent_t fork = nullptr;
     int device = 0;              // copies, so that destroying the batch never
@@ -927,7 +944,15 @@ static void batch_free(opo_batch *b)
             cudaStreamDestroy(g.stream);
         if (g.done)
             cudaEventDestroy(g.done);
+        if (g.graph)
+            cudaGraphExecDestroy(g.graph);
+        if (g.d_insts)
+            cudaFree(g.d_insts);
+        if (g.d_calls)
+            cudaFree(g.d_calls);
     }
+    if (b->capture)
+        cudaStreamDestroy(b->capture);
     for (cudaEvent_t e : b->ev)
         if (e)
             cudaEventDestroy(e);
@@ -977,27 +1002,52 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
         *th = threads > 0 ? threads : c->threads_req;
         *rt = c->rtpl_req;
     };
+    auto crystal_steps = [](const opo_ctx *c) {
+        std::vector<int> v;
+        for (int k = 0; k < c->ncry; k++)
+            v.push_back(c->cry[k].nz);
+        return v;
+    };
     for (int i = 0; i < count; i++) {
         opo_ctx *c = ctxs[i];
         int cl, th, rt;
         want(c, &cl, &th, &rt);
+        // the path: a plain request, or a size the fused kernels cannot hold
+        // with the automatic choice, runs in a plain group
+        FusedCfg fc{};
+        bool plain = c->path_req == OPO_PATH_PLAIN;
+        if (!plain && !fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, nl_variant(c), &fc)) {
+            if (c->path_req == OPO_PATH_FUSED) {
+                batch_free(b);
+                return OPO_E_UNSUPPORTED;
+            }
+            plain = true;
+        }
         int gi = -1;
-        for (size_t k = 0; k < b->groups.size(); k++) {
-            const opo_ctx *g0 = b->groups[k].ctxs[0];
+        for (size_t k = 0; k < b->groups.size() && gi < 0; k++) {
+            const BatchGroup &gg = b->groups[k];
+            const opo_ctx *g0 = gg.ctxs[0];
+            if (gg.plain != plain || g0->n != c->n || g0->F != c->F)
+                continue;
+            if (plain) {
+                if (gg.nzs == crystal_steps(c))
+                    gi = (int)k;
+                continue;
+            }
             int cl0, th0, rt0;
             want(g0, &cl0, &th0, &rt0);
-            if (g0->n == c->n && g0->F == c->F && nl_variant(g0) == nl_variant(c) && cl0 == cl &&
-                th0 == th && rt0 == rt)
+            if (nl_variant(g0) == nl_variant(c) && cl0 == cl && th0 == th && rt0 == rt)
                 gi = (int)k;
         }
         if (gi < 0) {
             b->groups.emplace_back();
             gi = (int)b->groups.size() - 1;
-            if (!fused_config(c->csz, c->F, c->F, c->n, c->n, cl, rt, th, nl_variant(c),
-                              &b->groups[gi].cfg)) {
-                batch_free(b);
-                return OPO_E_UNSUPPORTED;
-            }
+            BatchGroup &gg = b->groups[gi];
+            gg.plain = plain;
+            if (plain)
+                gg.nzs = crystal_steps(c);
+            else
+                gg.cfg = fc;
         }
         b->groups[gi].ctxs.push_back(c);
     }
@@ -1015,6 +1065,16 @@ int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32
             if (rc == OPO_OK)
                 rc = cuda_status(cudaEventCreateWithFlags(&gg.done, cudaEventDisableTiming));
         }
+    }
+    for (BatchGroup &gg : b->groups) {
+        if (rc != OPO_OK || !gg.plain)
+            continue;
+        const size_t k = gg.ctxs.size();
+        rc = cuda_status(cudaMalloc((void **)&gg.d_insts, sizeof(opo::PlainInst) * k));
+        if (rc == OPO_OK)
+            rc = cuda_status(cudaMalloc((void **)&gg.d_calls, sizeof(opo::PlainCall) * k));
+        if (rc == OPO_OK && !b->capture)
+            rc = cuda_status(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
     }
     if (rc != OPO_OK) {
         batch_free(b);
@@ -1123,6 +1183,71 @@ int batch_check_err(opo_batch *b)
         if (v)
             return OPO_E_NONFINITE;
     return OPO_OK;
+}
+
+// A member's state no longer matches the group it was put in (its crystals
+// or path request changed after the batch was made).
+bool group_stale(const BatchGroup &gg)
+{
+    for (const opo_ctx *c : gg.ctxs) {
+        if (gg.plain) {
+            if (c->path_req == OPO_PATH_FUSED || c->ncry != (int)gg.nzs.size())
+                return true;
+            for (int k = 0; k < c->ncry; k++)
+                if (c->cry[k].nz != gg.nzs[k])
+                    return true;
+        } else if (c->path_req == OPO_PATH_PLAIN || nl_variant(c) != gg.cfg.nl) {
+            return true;
+        }
+    }
+    return false;
+}
+
+// m round trips of a plain group on stream s: member descriptors (uploaded
+// when they changed), the per-call start, the captured round trip replayed m
+// times, the trace rows.
+int run_plain_group(opo_batch *b, BatchGroup &gg, int64_t m, cudaStream_t s)
+{
+    const int count = (int)gg.ctxs.size();
+    std::vector<opo::PlainInst> h(count);
+    for (int i = 0; i < count; i++)
+        plain_fill_inst(h[i], gg.ctxs[i]);
+    if (h.size() != gg.h_insts.size() ||
+        std::memcmp(h.data(), gg.h_insts.data(), sizeof(opo::PlainInst) * count) != 0) {
+        // the pageable source is staged before cudaMemcpyAsync returns
+        if (cudaMemcpyAsync(gg.d_insts, h.data(), sizeof(opo::PlainInst) * count,
+                            cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return OPO_E_CUDA;
+        gg.h_insts = h;
+    }
+    std::vector<opo::PlainCall> calls(count);
+    for (int i = 0; i < count; i++)
+        plain_fill_call(calls[i], gg.ctxs[i]);
+    if (cudaMemcpyAsync(gg.d_calls, calls.data(), sizeof(opo::PlainCall) * count,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return OPO_E_CUDA;
+    int rc = plain_batch_begin(gg.d_calls, count, s);
+    if (rc == OPO_OK && !gg.graph) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return OPO_E_CUDA;
+        rc = plain_batch_enqueue_roundtrip(gg.ctxs[0], gg.d_insts, count, b->capture);
+        cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+        if (rc == OPO_OK && e == cudaSuccess)
+            e = cudaGraphInstantiate(&gg.graph, g, 0);
+        if (g)
+            cudaGraphDestroy(g);
+        if (rc != OPO_OK || e != cudaSuccess) {
+            cudaGetLastError();
+            gg.graph = nullptr;
+            return OPO_E_CUDA;
+        }
+    }
+    for (int64_t i = 0; i < m && rc == OPO_OK; i++)
+        rc = cuda_status(cudaGraphLaunch(gg.graph, s));
+    if (rc == OPO_OK)
+        rc = plain_batch_finalize(gg.d_calls, count, m, s);
+    return rc;
 }
 
 } // namespace
@@ -1235,12 +1360,15 @@ int opo_batch_run(opo_batch *b, int64_t m)
         return OPO_E_CUDA;
     cudaStream_t s = c0->stream;
     const int count = (int)b->ctxs.size();
-    for (const BatchGroup &gg : b->groups)
+    for (const BatchGroup &gg : b->groups) {
+        if (group_stale(gg))
+            return OPO_E_STATE;
         for (opo_ctx *c : gg.ctxs) {
-            int rc = begin_call(c, m, gg.cfg.cluster, false);
+            int rc = begin_call(c, m, gg.plain ? 1 : gg.cfg.cluster, false);
             if (rc != OPO_OK)
                 return rc;
         }
+    }
     for (int i = 0; i < count; i++) {
         opo_ctx *c = b->ctxs[i];
         if (c->stream != s) {
@@ -1249,17 +1377,20 @@ int opo_batch_run(opo_batch *b, int64_t m)
         }
     }
     int rc = OPO_OK;
+    auto run_group = [&](BatchGroup &gg, cudaStream_t gs) {
+        return gg.plain ? run_plain_group(b, gg, m, gs)
+                        : fused_run(gg.ctxs.data(), (int)gg.ctxs.size(), gg.cfg, m, gs);
+    };
     if (m > 0) {
         if (b->groups.size() == 1) {
-            BatchGroup &gg = b->groups[0];
-            rc = fused_run(gg.ctxs.data(), (int)gg.ctxs.size(), gg.cfg, m, s);
+            rc = run_group(b->groups[0], s);
         } else {
             cudaEventRecord(b->fork, s);
             for (BatchGroup &gg : b->groups) {
                 if (rc != OPO_OK)
                     break;
                 cudaStreamWaitEvent(gg.stream, b->fork, 0);
-                rc = fused_run(gg.ctxs.data(), (int)gg.ctxs.size(), gg.cfg, m, gg.stream);
+                rc = run_group(gg, gg.stream);
                 cudaEventRecord(gg.done, gg.stream);
                 cudaStreamWaitEvent(s, gg.done, 0);
             }
@@ -1269,9 +1400,9 @@ int opo_batch_run(opo_batch *b, int64_t m)
         for (opo_ctx *c : gg.ctxs) {
             c->rt += m;
             c->last_M = m;
-            c->last_parts = gg.cfg.cluster;
-            c->last_path = OPO_PATH_FUSED;
-            c->last_cluster = gg.cfg.cluster;
+            c->last_parts = gg.plain ? 1 : gg.cfg.cluster;
+            c->last_path = gg.plain ? OPO_PATH_PLAIN : OPO_PATH_FUSED;
+            c->last_cluster = gg.plain ? 0 : gg.cfg.cluster;
         }
     for (int i = 0; i < count; i++) {
         opo_ctx *c = b->ctxs[i];

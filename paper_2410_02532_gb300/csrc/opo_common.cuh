@@ -176,12 +176,13 @@ __device__ __forceinline__ void nl_prod(const V *a, V e, bool use_e, V *p)
     }
 }
 
-// y + g (i p) for real g (explicit multiply-adds: every compiled copy of the
-// RK4 step rounds alike, whatever the surrounding code)
+// y + g (i p) for real g (explicit fused multiply-adds: left to the
+// compiler, y - g p may be contracted in one kernel and not in another, and
+// two kernels running the same step would not round alike)
 template <class V>
 __device__ __forceinline__ V add_ig(V y, typename cscal<V>::type g, V p)
 {
-    return cmk<V>(y.x - g * p.y, y.y + g * p.x);
+    return cmk<V>(fmad_(-g, p.y, y.x), fmad_(g, p.x, y.y));
 }
 
 template <int F, int EM, class V>

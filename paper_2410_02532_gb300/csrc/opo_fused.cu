@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     double p2 = (double)cabs2(v);
                     int kk = (k < (n >> 1)) ? k : k - n;
                     acc[3] += p2;
-                    acc[4] += (double)kk * p2;
+                    acc[4] = __fma_rn((double)kk, p2, acc[4]);
                 }
             } else {
                 fac = dsm ? Dsm[(seq << logQ) + k2] : gDk[(size_t)f * n + k];
@@ -543,6 +543,8 @@ void fill_desc(InstDesc &d, const opo_ctx *c)
         d.kerr_g[i] = c->dv.kerr_g[i];
     d.cry = c->d_cry;
     d.ncry = c->ncry;
+    d.xg1 = c->d_scratch;
+    d.xg2 = c->d_xg;
 }
 
 int fused_run(opo_ctx *const *ctxs, int count, const FusedCfg &cfg, int64_t m, cudaStream_t s)

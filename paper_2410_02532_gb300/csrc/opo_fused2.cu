@@ -22,6 +22,37 @@ int dispatch(int op, bool ip, int nl, bool dbl, int F, int logn, const InstDesc 
                                         chunk, last, s);
 }
 
+// In place with the exchange through global memory: one buffer (X and Y
+// alias), three FP32 fields at 2^17 or FP64 at 2^16, 16-CTA clusters.
+bool xg_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedCfg *out)
+{
+    if (!((logn == 17 && !dbl) || (logn == 16 && dbl)) || C != 16)
+        return false;
+    const int LP = logn / 2, LQ = logn - LP;
+    const int nc = (1 << logn) / C;
+    const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
+    const int LS = (logn + 1) / 2;
+    // one buffer; stage twiddles (2P + 2Q); W_N halves (lo, hi)
+    const size_t el = (size_t)F * nc + 2 * (1 << LP) + 2 * (1 << LQ) + (1 << LS) +
+                      ((1 << logn) >> LS);
+    const size_t sm = el * csz + 32 * kNslot * sizeof(double);
+    if (sm > 227 * 1024)
+        return false;
+    const int maxT = dbl ? 256 : 384;
+    const int threads = threads_req > 0 ? threads_req : 256;
+    if (threads < 32 || threads > maxT || (threads & 31))
+        return false;
+    if (dispatch(1, true, nl, dbl, F, logn, nullptr, 0, C, threads, sm, false, 0, 0, 0, nullptr) < 1)
+        return false;
+    out->cluster = C;
+    out->threads = threads;
+    out->disp_in_smem = false;
+    out->smem = sm;
+    out->kernel = 4;
+    out->nl = nl;
+    return true;
+}
+
 // In-place variant: X and Y only, dispersion factors from L2.
 bool ip_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
@@ -123,7 +154,9 @@ bool three_buffer_config(bool dbl, int nl, int F, int logn, int C, int threads_r
 // memory, else the in-place form (cheaper addressing, same passes).
 bool fused2_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedCfg *out)
 {
-    if (logn < 12 || logn > 16 || (logn == 16 && dbl))
+    if ((logn == 17 && !dbl) || (logn == 16 && dbl))
+        return xg_config(dbl, nl, F, logn, C, threads_req, out);
+    if (logn < 12 || logn > 16)
         return false;
     FusedCfg a, b;
     const bool ok_a = three_buffer_config(dbl, nl, F, logn, C, threads_req, &a);
@@ -142,14 +175,14 @@ bool fused2_config(bool dbl, int nl, int F, int logn, int C, int threads_req, Fu
 
 int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg)
 {
-    return dispatch(1, cfg.kernel == 3, cfg.nl, dbl, F, logn, nullptr, 0, cfg.cluster,
+    return dispatch(1, cfg.kernel >= 3, cfg.nl, dbl, F, logn, nullptr, 0, cfg.cluster,
                     cfg.threads, cfg.smem, cfg.disp_in_smem, 0, 0, 0, nullptr);
 }
 
 int fused2_launch(bool dbl, int F, int logn, const InstDesc *dd, int count, const FusedCfg &cfg,
                   int r_base, int chunk, int last, cudaStream_t s)
 {
-    return dispatch(0, cfg.kernel == 3, cfg.nl, dbl, F, logn, dd, count, cfg.cluster,
+    return dispatch(0, cfg.kernel >= 3, cfg.nl, dbl, F, logn, dd, count, cfg.cluster,
                     cfg.threads, cfg.smem, cfg.disp_in_smem, r_base, chunk, last, s);
 }
 

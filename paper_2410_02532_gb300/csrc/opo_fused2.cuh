@@ -78,24 +78,43 @@ constexpr int kF2MaxThreads = IP ? F2IpTraits<T>::kMaxThreads : F2Traits<T>::kMa
 // of every field in one thread: 255 registers and block A at half speed);
 // the 32-point stages go to the column push and the last inverse stage.
 constexpr int f2_col_a2(int LP) { return LP == 8 ? 5 : (LP + 1) / 2; }
+// Row split [Rb1, Rb2] = [2^B1, 2^B2] of a Q = 2^LQ row transform: B2 =
+// ceil(LQ/2), except Q = 512, split [32, 16] so that a block-B item keeps 16
+// values (and 16 factors) as at Q = 256; the 32-point stages go to the row
+// stage before block B and the inverse push.
+constexpr int f2_row_b2(int LQ) { return LQ == 9 ? 4 : (LQ + 1) / 2; }
 
-// P = 256 (N = 2^16): the 32-point column stages need more than 128
-// registers: at most 384 threads
+// P = 256 (N = 2^16, 2^17): the 32-point column stages need more than 128
+// registers: at most 384 threads in FP32, 256 in FP64 (up to 255 registers)
 template <class T, bool IP, int LP>
-constexpr int kF2MaxThreadsL = LP >= 8 ? 384 : kF2MaxThreads<T, IP>;
+constexpr int kF2MaxThreadsL = LP >= 8 ? (sizeof(T) == 8 ? 256 : 384) : kF2MaxThreads<T, IP>;
 
 // NL: the nonlinear-step variant (kNlChi2, kNlKerr, kNlChi2NoDk), each a
 // separate instantiation so that every kernel carries only the arithmetic
-// (and the registers) its instances need
-template <class T, int F, int LP, int LQ, bool IP, int NL>
+// (and the registers) its instances need.
+//
+// XG (with IP): the exchange between CTAs goes through two global buffers of
+// the instance (F N values each, L2-resident) instead of the owners' shared
+// memory, and X and Y are one buffer: a CTA holds only N/C points per field
+// once, so three FP32 fields at N = 2^17, or FP64 at 2^16, fit a 16-CTA
+// cluster.  The forward push writes G1 in the natural row-major order of the
+// frequency rows, [f][k1][n2]; after the cluster barrier each CTA's first row
+// stage reads its rows from G1 into Y (X's space: every CTA has read its own
+// columns before the barrier).  The inverse push writes G2 in the time-domain
+// order [f][n1][n2]; after the second barrier the first inverse column stage
+// reads its columns from G2 into X.  Each buffer is written only between the
+// barrier that follows its last reads and the barrier that precedes its next
+// reads, so the two cluster barriers per z-step still suffice.
+template <class T, int F, int LP, int LQ, bool IP, int NL, bool XG = false>
 __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     k_fused2(const InstDesc *__restrict__ descs, int r_base, int M, int write_out, int disp_smem)
 {
+    static_assert(!XG || IP, "the exchange through global memory uses the in-place layouts");
     constexpr bool KR = NL == kNlKerr;
     using V = cv<T>;
     constexpr int P = 1 << LP, Q = 1 << LQ, LN = LP + LQ, N = 1 << LN;
     constexpr int A2 = f2_col_a2(LP), A1 = LP - A2; // columns [Ra1, Ra2]
-    constexpr int B2 = (LQ + 1) / 2, B1 = LQ - B2; // rows    [Rb1, Rb2]
+    constexpr int B2 = f2_row_b2(LQ), B1 = LQ - B2; // rows    [Rb1, Rb2]
     constexpr int Ra1 = 1 << A1, Ra2 = 1 << A2, Rb1 = 1 << B1, Rb2 = 1 << B2;
     constexpr int LS = (LN + 1) / 2; // W_N^a = hi[a >> LS] lo[a & (2^LS - 1)]
     constexpr int SW = F2Traits<T>::kSwz;
@@ -112,7 +131,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *X = reinterpret_cast<V *>(smem_raw);
-    V *Y = X + F * NC;
+    V *Y = XG ? X : X + F * NC;
     V *S = IP ? nullptr : Y + F * NC;
     V *Dsm = IP ? Y + F * NC : S + F * NC;
     // stage twiddles W^{r j}, indexed [r][j] with j the butterfly index that
@@ -175,6 +194,10 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     const V *gtw = (const V *)dg.tw;
     double *obs = dg.obs;
     int *err = dg.err;
+    V *G1 = (V *)dg.xg1; // XG: forward exchange, [f][k1][n2]
+    V *G2 = (V *)dg.xg2; // XG: inverse exchange, [f][n1][n2]
+    (void)G1;
+    (void)G2;
 
     // W_P^e = gtw[e << LQ], W_Q^e = gtw[e << LP]
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -572,7 +595,16 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             // W_N^{n2 k1} for k1 = j + r Ra1: base W_N^{n2 j} times step^r
             const V step = twN((unsigned)(n2 * Ra1));
             V w = twN((unsigned)(n2 * j));
-            if (tab2) {
+            if constexpr (XG) {
+                // row k1 = j + r Ra1 of G1, column n2: consecutive lanes write
+                // consecutive n2
+                V *g = G1 + (size_t)f * N + (size_t)j * Q + n2;
+#pragma unroll
+                for (int r = 0; r < Ra2; r++) {
+                    __stcg(g + (size_t)r * Ra1 * Q, cmul(v[r], w));
+                    w = cmul(w, step);
+                }
+            } else if (tab2) {
                 const unsigned a0 = (unsigned)(sizeof(V) * RI(f, j, n2));
 #pragma unroll
                 for (int r = 0; r < Ra2; r++) {
@@ -600,7 +632,24 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             row = rest & (Pc - 1);
             f = rest >> logPc;
         };
-        if constexpr (IP) {
+        if constexpr (XG) {
+            // the CTA's rows from G1 (consecutive lanes read consecutive
+            // elements of a row), written to Y: no in-place hazard
+            for (int u = threadIdx.x; u < items; u += blockDim.x) {
+                int j, row, f;
+                dec(u, j, row, f);
+                const V *src = G1 + (size_t)f * N + (size_t)((c << logPc) + row) * Q + j;
+                V v[Rb1];
+#pragma unroll
+                for (int r = 0; r < Rb1; r++)
+                    v[r] = __ldcg(src + r * Rb2);
+                dft_r<Rb1, -1>(v);
+                const unsigned a1 = ipo(Y, RI(f, row, j * Rb1));
+#pragma unroll
+                for (int r = 0; r < Rb1; r++)
+                    ipx(a1, r) = v[r];
+            }
+        } else if constexpr (IP) {
 #pragma unroll 1
             for (int base = 0; base < items; base += blockDim.x) {
                 const int u0 = base + threadIdx.x;
@@ -701,7 +750,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
                 if (cav && f == 1 && own) {
                     double p2 = (double)cabs2(v[r]);
                     acc[3] += p2;
-                    acc[4] += (double)((k < N / 2) ? k : k - N) * p2;
+                    acc[4] = __fma_rn((double)((k < N / 2) ? k : k - N), p2, acc[4]);
                 }
                 v[r] = cmul(v[r], d);
             }
@@ -754,7 +803,7 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
         const int items = F * Pc * Rb2;
         for (int u = threadIdx.x; u < items; u += blockDim.x) {
             int j, row, f;
-            if constexpr (IP) {
+            if constexpr (IP && !XG) {
                 row = u & (Pc - 1);
                 const int rest = u >> logPc;
                 j = rest & (Rb2 - 1);
@@ -789,7 +838,16 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
             step.y = -step.y;
             V w = twN((unsigned)(k1 * j));
             w.y = -w.y;
-            if (tab5) {
+            if constexpr (XG) {
+                // row n1 = k1 of G2, columns n2 = j + r Rb2: consecutive lanes
+                // write consecutive n2
+                V *g = G2 + (size_t)f * N + (size_t)k1 * Q + j;
+#pragma unroll
+                for (int r = 0; r < Rb1; r++) {
+                    __stcg(g + r * Rb2, cmul(v[r], w));
+                    w = cmul(w, step);
+                }
+            } else if (tab5) {
                 const unsigned a0 = (unsigned)(sizeof(V) * CI(f, k1, j));
 #pragma unroll
                 for (int r = 0; r < Rb1; r++) {
@@ -811,7 +869,25 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     // ---- phase 6: inverse column stage 1, X -> S (in place on X for IP)
     auto phase6 = [&]() {
         const int items = F * Qc * Ra1;
-        if constexpr (IP) {
+        if constexpr (XG) {
+            // the CTA's columns from G2 (consecutive lanes read consecutive
+            // columns of a row), written to X: no in-place hazard
+            for (int u = threadIdx.x; u < items; u += blockDim.x) {
+                const int b = u & (Qc - 1);
+                const int rest = u >> logQc;
+                const int j = rest & (Ra1 - 1), f = rest >> A1;
+                const V *src = G2 + (size_t)f * N + (size_t)j * Q + (c << logQc) + b;
+                V v[Ra2];
+#pragma unroll
+                for (int r = 0; r < Ra2; r++)
+                    v[r] = __ldcg(src + (size_t)r * Ra1 * Q);
+                dft_r<Ra2, 1>(v);
+                const unsigned a1 = ipo(X, cidx_ip(f, j * Ra2, b));
+#pragma unroll
+                for (int r = 0; r < Ra2; r++)
+                    ipx(a1, r) = v[r];
+            }
+        } else if constexpr (IP) {
 #pragma unroll 1
             for (int base = 0; base < items; base += blockDim.x) {
                 const int u0 = base + threadIdx.x;
@@ -853,16 +929,24 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     };
 
     // forward transform (after block A), frequency visit, inverse up to S
+    // XG: the pushes went to global memory; a device-scope fence before the
+    // cluster barrier makes them visible to the other CTAs (which read them
+    // past L1)
+    auto xsync = [&]() {
+        if constexpr (XG)
+            __threadfence();
+        cluster.sync();
+    };
     auto middle = [&](auto cav_tag, double *acc, int kc) {
         __syncthreads();
         phase2();
-        cluster.sync();
+        xsync();
         phase3();
         __syncthreads();
         block_b(cav_tag, acc, kc);
         __syncthreads();
         phase5();
-        cluster.sync();
+        xsync();
         phase6();
         __syncthreads();
     };
@@ -917,11 +1001,11 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, IP, LP>, 1)
     }
 }
 
-template <class T, int F, int LP, int LQ, bool IP, int NL>
+template <class T, int F, int LP, int LQ, bool IP, int NL, bool XG>
 int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool disp_smem,
              int r_base, int chunk, int last, cudaStream_t s)
 {
-    auto kern = k_fused2<T, F, LP, LQ, IP, NL>;
+    auto kern = k_fused2<T, F, LP, LQ, IP, NL, XG>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t lc = {};
@@ -940,10 +1024,10 @@ int launch_t(const InstDesc *dd, int count, int C, int threads, size_t sm, bool 
     return e == cudaSuccess ? OPO_OK : OPO_E_CUDA;
 }
 
-template <class T, int F, int LP, int LQ, bool IP, int NL>
+template <class T, int F, int LP, int LQ, bool IP, int NL, bool XG>
 int max_active_t(int C, int threads, size_t sm)
 {
-    auto kern = k_fused2<T, F, LP, LQ, IP, NL>;
+    auto kern = k_fused2<T, F, LP, LQ, IP, NL, XG>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t lc = {};
@@ -987,49 +1071,78 @@ OPO_F2_DISPATCH_NL_DECL(dispatch_f64_f2_kerr);
 OPO_F2_DISPATCH_NL_DECL(dispatch_f32_f3_nodk);
 OPO_F2_DISPATCH_NL_DECL(dispatch_f32_f2_nodk);
 
-#define OPO_F2_ONE(T, F, LP, LQ, IP, NL)                                                         \
-    return op == 0 ? launch_t<T, F, LP, LQ, IP, NL>(dd, count, C, threads, sm, ds, r_base,       \
-                                                    chunk, last, s)                              \
-                   : max_active_t<T, F, LP, LQ, IP, NL>(C, threads, sm)
+// Launch (op 0) or occupancy query (op 1) of one instantiation.
+template <class T, int F, int LP, int LQ, bool IP, int NL, bool XG>
+int one_t(int op, const InstDesc *dd, int count, int C, int threads, size_t sm, bool ds,
+          int r_base, int chunk, int last, cudaStream_t s)
+{
+    return op == 0 ? launch_t<T, F, LP, LQ, IP, NL, XG>(dd, count, C, threads, sm, ds, r_base,
+                                                        chunk, last, s)
+                   : max_active_t<T, F, LP, LQ, IP, NL, XG>(C, threads, sm);
+}
 
-// every size for one (T, F, NL)
-#define OPO_F2_SIZES(T, F, NL)                                                                   \
-    if (ip) {                                                                                    \
-        switch (logn) {                                                                          \
-        case 12:                                                                                 \
-            OPO_F2_ONE(T, F, 6, 6, true, NL);                                                    \
-        case 13:                                                                                 \
-            OPO_F2_ONE(T, F, 6, 7, true, NL);                                                    \
-        case 14:                                                                                 \
-            OPO_F2_ONE(T, F, 7, 7, true, NL);                                                    \
-        case 15:                                                                                 \
-            OPO_F2_ONE(T, F, 7, 8, true, NL);                                                    \
-        case 16:                                                                                 \
-            if constexpr (sizeof(T) == 4) {                                                      \
-                OPO_F2_ONE(T, F, 8, 8, true, NL);                                                \
-            }                                                                                    \
-            return op == 0 ? OPO_E_UNSUPPORTED : 0;                                              \
-        default:                                                                                 \
-            return op == 0 ? OPO_E_UNSUPPORTED : 0;                                              \
-        }                                                                                        \
-    }                                                                                            \
-    switch (logn) {                                                                              \
-    case 12:                                                                                     \
-        OPO_F2_ONE(T, F, 6, 6, false, NL);                                                       \
-    case 13:                                                                                     \
-        OPO_F2_ONE(T, F, 6, 7, false, NL);                                                       \
-    case 14:                                                                                     \
-        OPO_F2_ONE(T, F, 7, 7, false, NL);                                                       \
-    case 15:                                                                                     \
-        OPO_F2_ONE(T, F, 7, 8, false, NL);                                                       \
-    case 16:                                                                                     \
-        if constexpr (sizeof(T) == 4) {                                                          \
-            OPO_F2_ONE(T, F, 8, 8, false, NL);                                                   \
-        }                                                                                        \
-        return op == 0 ? OPO_E_UNSUPPORTED : 0;                                                  \
-    default:                                                                                     \
-        return op == 0 ? OPO_E_UNSUPPORTED : 0;                                                  \
+// Every size for one (T, F, NL).  A function template, so that the branches
+// `if constexpr` discards (sizes a precision does not have) are not compiled.
+// In place: 2^12..2^16 exchange through the owners' shared memory; three
+// FP32 fields at 2^17 and FP64 at 2^16 exchange through global memory.
+template <class T, int F, int NL>
+int sizes_t(int op, bool ip, int logn, const InstDesc *dd, int count, int C, int threads,
+            size_t sm, bool ds, int r_base, int chunk, int last, cudaStream_t s)
+{
+    constexpr bool F32 = sizeof(T) == 4;
+    const int none = op == 0 ? OPO_E_UNSUPPORTED : 0;
+#define OPO_F2_ONE(LP, LQ, IP, XG)                                                               \
+    return one_t<T, F, LP, LQ, IP, NL, XG>(op, dd, count, C, threads, sm, ds, r_base, chunk,     \
+                                           last, s)
+    if (ip) {
+        switch (logn) {
+        case 12:
+            OPO_F2_ONE(6, 6, true, false);
+        case 13:
+            OPO_F2_ONE(6, 7, true, false);
+        case 14:
+            OPO_F2_ONE(7, 7, true, false);
+        case 15:
+            OPO_F2_ONE(7, 8, true, false);
+        case 16:
+            if constexpr (F32) {
+                OPO_F2_ONE(8, 8, true, false);
+            } else {
+                OPO_F2_ONE(8, 8, true, true);
+            }
+        case 17:
+            if constexpr (F32) {
+                OPO_F2_ONE(8, 9, true, true);
+            } else {
+                return none;
+            }
+        default:
+            return none;
+        }
     }
+    switch (logn) {
+    case 12:
+        OPO_F2_ONE(6, 6, false, false);
+    case 13:
+        OPO_F2_ONE(6, 7, false, false);
+    case 14:
+        OPO_F2_ONE(7, 7, false, false);
+    case 15:
+        OPO_F2_ONE(7, 8, false, false);
+    case 16:
+        if constexpr (F32) {
+            OPO_F2_ONE(8, 8, false, false);
+        } else {
+            return none;
+        }
+    default:
+        return none;
+    }
+#undef OPO_F2_ONE
+}
+
+#define OPO_F2_SIZES(T, F, NL)                                                                   \
+    return sizes_t<T, F, NL>(op, ip, logn, dd, count, C, threads, sm, ds, r_base, chunk, last, s);
 
 // the general chi(2) sizes, and the entry point that forwards the other
 // variants to their translation units (FP64 has no dk = 0 variant)

@@ -34,6 +34,8 @@ struct InstDesc {
     double kerr_g[9];  // their coefficients G_xy, row-major
     const CryDesc *cry; // every crystal of the round trip (cry[0]: the fields above)
     int ncry;
+    void *xg1, *xg2;   // F*N each: exchange buffers of the form that exchanges
+                       // through global memory (null where unused)
 };
 
 // Observables of every instance and slot of the call: output power
@@ -85,7 +87,7 @@ static __device__ __forceinline__ void block_reduce5(double *v, double *red)
 // Fill one descriptor from a context (host).
 void fill_desc(InstDesc &d, const opo_ctx *c);
 
-// opo_fused2.cu: the size-specialised kernel (N = 2^12 .. 2^15, one size and
+// opo_fused2.cu: the size-specialised kernel (N = 2^12 .. 2^17, one size and
 // field count per launch).
 bool fused2_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedCfg *out);
 int fused2_max_active(bool dbl, int F, int logn, const FusedCfg &cfg);

@@ -65,8 +65,44 @@ struct CrystalState {
 // products).
 constexpr int kNlChi2 = 0, kNlKerr = 1, kNlChi2NoDk = 2;
 
+// Cavity elements of the plain path's time-domain kernel: mirror
+// sqrt(R) e^{i delta} and the EOM, on resonant fields.
+struct PlainCav {
+    double bc_re[3], bc_im[3];
+    double eom_beta, eom_f, t_rt, dt;
+    unsigned resmask;
+    int eom;
+};
+
+// One member of a batched plain-path launch (a device array of these, one per
+// instance; the batch kernels take instance blockIdx.z).  The same kernels'
+// bodies run a lone context, so a member advances exactly as it would alone.
+struct PlainInst {
+    void *fields, *out, *scratch, *hist;
+    const void *pump, *gdd, *tw;
+    const CryDesc *cry;   // the instance's crystals (device copy)
+    DevCtl *ctl;
+    NsPump ns;
+    PlainCav cav;
+    double outscale[3];   // sqrt(1 - R) on resonant fields, else 1
+    int spec_all;         // the cavity visit transforms every field (GDD or
+                          // delay on a resonant field), else a signal copy
+};
+
+// Per-call values of a batch member: start of the call (round-trip counter,
+// observable storage) and the trace rows it finalizes.
+struct PlainCall {
+    DevCtl *ctl;
+    double *obs, *trace;
+    int64_t rt0;
+    double outscale2[3], pscale[3];
+    double inv_n, t_window;
+    int F;
+};
+
 struct FusedCfg {
-    int kernel = 1;      // 1: generic, 2: size-specialised, 3: size-specialised in place
+    int kernel = 1;      // 1: generic, 2: size-specialised, 3: size-specialised in place,
+                         // 4: in place with the exchange through global memory
     int nl = 0;          // kNl* variant (kernels 2, 3 instantiate each)
     int cluster;         // CTAs per instance
     int threads;         // threads per CTA
@@ -98,7 +134,11 @@ struct opo_ctx {
     // device memory (complex arrays in the context's precision)
     void *d_fields = nullptr;  // F*N intracavity state
     void *d_out = nullptr;     // F*N output-coupled fields of the last round trip
-    void *d_scratch = nullptr; // F*N FFT intermediate of the plain path
+    void *d_scratch = nullptr; // F*N FFT intermediate of the plain path; also the
+                               // forward exchange buffer of the fused form that
+                               // exchanges through global memory
+    void *d_xg = nullptr;      // F*N inverse exchange buffer of that form (the
+                               // sizes that need it only)
     void *d_pump = nullptr;    // N input pump
     void *d_disp = nullptr;    // F*N dispersion factors / N, natural order
     void *d_gdd = nullptr;     // F*N cavity spectral factors / N, natural order
@@ -128,6 +168,7 @@ struct opo_ctx {
     int last_path = OPO_PATH_PLAIN, last_cluster = 0;
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
+    uint64_t gen = 0;          // bumped whenever crystals, cavity or history change
 };
 
 namespace opo {
@@ -152,6 +193,15 @@ int setup_pass_tables(void *tw, void *disp, void *ekz, int n, int F, bool dbl,
 // opo_plain.cu
 void plain_prepare(opo_ctx *c);
 int plain_enqueue_roundtrip(opo_ctx *c, cudaStream_t s);
+// the batched plain path: members' descriptors, one captured round trip of
+// every member (c0 gives N, F, precision and the crystals' step counts, the
+// same in every member), and the per-call start and trace of every member
+void plain_fill_inst(PlainInst &p, const opo_ctx *c);
+void plain_fill_call(PlainCall &p, const opo_ctx *c);
+int plain_batch_enqueue_roundtrip(const opo_ctx *c0, const PlainInst *d_insts, int count,
+                                  cudaStream_t s);
+int plain_batch_begin(const PlainCall *d_calls, int count, cudaStream_t s);
+int plain_batch_finalize(const PlainCall *d_calls, int count, int64_t M, cudaStream_t s);
 // one crystal pass of the plain kernels on caller-given buffers
 int plain_pass_raw(void *fields, void *scratch, const void *tw, const void *disp, const void *ekz,
                    int n, int F, int nz, const double kappa[3], double h, bool use_dk,

@@ -11,6 +11,16 @@
 // W_N^{n2 k1} written to scratch, then Q-point row transforms written back in
 // natural order.  Each kernel transforms a batch of columns or rows in shared
 // memory with Stockham stages of radix 2..16.
+//
+// Two launch forms share every kernel body: one instance per launch (a
+// context's own graph; the allocation-free pass), and a batch in which each
+// launch runs the same operation for every member, member blockIdx.z, with
+// the member's pointers and parameters read from a device descriptor
+// (PlainInst).  The paper's design is the first form; the second is that
+// design over many instances at once.  Per element both do the same
+// arithmetic, so a member advances bit for bit as it would alone.
+#include <algorithm>
+
 #include "opo_common.cuh"
 #include "opo_internal.h"
 
@@ -19,14 +29,17 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// ------------------------------------------------------------- bodies ----
+// Each body works on one instance; elementwise bodies stride over
+// blockIdx.x / gridDim.x.
+
 // Round-trip entry: the input pump (table, or the ns-pulsed pump read at
 // this round trip) replaces a non-resonant pump and is added to a resonant
 // one; non-resonant signal/idler restart from zero.
 template <class T>
-__global__ void k_entry(cv<T> *fields, const cv<T> *pump, int n, int F, unsigned resmask,
-                        NsPump ns, const DevCtl *ctl)
+__device__ __forceinline__ void entry_body(cv<T> *fields, const cv<T> *pump, int n, int F,
+                                           unsigned resmask, const NsPump &ns, int64_t m)
 {
-    const int64_t m = ctl->rt0 + ctl->slot;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F * n; i += gridDim.x * blockDim.x) {
         const int x = i / n;
         const bool res = (resmask >> x) & 1u;
@@ -39,26 +52,12 @@ __global__ void k_entry(cv<T> *fields, const cv<T> *pump, int n, int F, unsigned
     }
 }
 
-// Kerr coefficients G_xy (row-major) in the field precision.
-template <class T> struct KerrG {
-    T g[9];
-};
-
-template <class T>
-KerrG<T> kerr_g(const double *g)
-{
-    KerrG<T> k;
-    for (int i = 0; i < 9; i++)
-        k.g[i] = (T)g[i];
-    return k;
-}
-
+// One RK4 step of h = dz/2 on every point (the nonlinear half step).
 template <class T, int F>
-__global__ void k_rk4(cv<T> *fields, int n, const cv<T> *ekz, int q0, T h, T k0, T k1, T k2,
-                      bool use_e, bool kerr, KerrG<T> G)
+__device__ __forceinline__ void rk4_body(cv<T> *fields, int n, const cv<T> *ekz, int q0, T h,
+                                         const T *kap, bool use_e, bool kerr, const T *G)
 {
     using V = cv<T>;
-    const T kap[3] = {k0, k1, k2};
     V e0 = ekz[q0], e1 = ekz[q0 + 1], e2 = ekz[q0 + 2];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         V y[F];
@@ -66,7 +65,7 @@ __global__ void k_rk4(cv<T> *fields, int n, const cv<T> *ekz, int q0, T h, T k0,
         for (int x = 0; x < F; x++)
             y[x] = fields[(size_t)x * n + j];
         if (kerr)
-            rk4_point_kerr<F>(y, e0, e1, e2, kap, h, use_e, G.g);
+            rk4_point_kerr<F>(y, e0, e1, e2, kap, h, use_e, G);
         else
             rk4_point<F>(y, e0, e1, e2, kap, h, use_e);
 #pragma unroll
@@ -75,20 +74,19 @@ __global__ void k_rk4(cv<T> *fields, int n, const cv<T> *ekz, int q0, T h, T k0,
     }
 }
 
-// Column pass: grid (Q/B, fields).  Loads columns n2 in [g B, g B + B) of
-// x[Q n1 + n2], transforms over n1, multiplies W_N^{DIR n2 k1} and writes
-// y[k1 Q + n2].
+// Column pass of one field: loads columns n2 in [cb B, cb B + B) of
+// src[Q n1 + n2], transforms over n1, multiplies W_N^{DIR n2 k1} and writes
+// dst[k1 Q + n2].
 template <class T, int DIR>
-__global__ void k_fft_cols(const cv<T> *__restrict__ in, cv<T> *__restrict__ out, int n, int P,
-                           int Q, int logP, int logn, int B, const cv<T> *__restrict__ tw)
+__device__ __forceinline__ void fft_cols_body(const cv<T> *__restrict__ src, cv<T> *__restrict__ dst,
+                                              int n, int P, int Q, int logP, int logn, int B,
+                                              const cv<T> *__restrict__ tw, int cb)
 {
     using V = cv<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *s0 = reinterpret_cast<V *>(smem_raw);
     V *s1 = s0 + B * P;
-    const V *src = in + (size_t)blockIdx.y * n;
-    V *dst = out + (size_t)blockIdx.y * n;
-    const int n2b = blockIdx.x * B;
+    const int n2b = cb * B;
     for (int i = threadIdx.x; i < B * P; i += blockDim.x) {
         int b = i % B, n1 = i / B;
         s0[n1 * B + b] = src[(size_t)n1 * Q + n2b + b];
@@ -119,20 +117,19 @@ __global__ void k_fft_cols(const cv<T> *__restrict__ in, cv<T> *__restrict__ out
     }
 }
 
-// Row pass: grid (P/B, fields).  Loads rows k1 in [h B, h B + B) of
-// y[k1 Q + n2], transforms over n2 and writes X[k1 + P k2].
+// Row pass of one field: loads rows k1 in [rb B, rb B + B) of
+// src[k1 Q + n2], transforms over n2 and writes dst[k1 + P k2].
 template <class T, int DIR>
-__global__ void k_fft_rows(const cv<T> *__restrict__ in, cv<T> *__restrict__ out, int n, int P,
-                           int Q, int logQ, int logn, int B, const cv<T> *__restrict__ tw)
+__device__ __forceinline__ void fft_rows_body(const cv<T> *__restrict__ src, cv<T> *__restrict__ dst,
+                                              int n, int P, int Q, int logQ, int logn, int B,
+                                              const cv<T> *__restrict__ tw, int rb)
 {
     using V = cv<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lp = Q + 1; // padded row stride
     V *s0 = reinterpret_cast<V *>(smem_raw);
     V *s1 = s0 + B * Lp;
-    const V *src = in + (size_t)blockIdx.y * n;
-    V *dst = out + (size_t)blockIdx.y * n;
-    const int k1b = blockIdx.x * B;
+    const int k1b = rb * B;
     for (int i = threadIdx.x; i < B * Q; i += blockDim.x) {
         int b = i / Q, n2 = i % Q;
         s0[b * Lp + n2] = src[(size_t)(k1b + b) * Q + n2];
@@ -160,7 +157,7 @@ __global__ void k_fft_rows(const cv<T> *__restrict__ in, cv<T> *__restrict__ out
 }
 
 template <class T>
-__global__ void k_mul_table(cv<T> *a, const cv<T> *__restrict__ tab, int total)
+__device__ __forceinline__ void mul_table_body(cv<T> *a, const cv<T> *__restrict__ tab, int total)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
         a[i] = cmul(a[i], tab[i]);
@@ -183,13 +180,12 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return t;
 }
 
-// One block per field: Sum |A_x|^2 of the post-crystal field into the raw
-// observable slot of this round trip; a non-finite sum sets the error word.
+// Sum |A_x|^2 of the post-crystal field x into the raw observable slot of
+// this round trip; a non-finite sum sets the error word.
 template <class T>
-__global__ void k_power_sums(const cv<T> *fields, int n, DevCtl *ctl)
+__device__ __forceinline__ void power_body(const cv<T> *fields, int n, int x, DevCtl *ctl)
 {
     __shared__ double red[32];
-    const int x = blockIdx.x;
     double s = 0.0;
     for (int j = threadIdx.x; j < n; j += blockDim.x)
         s += (double)cabs2(fields[(size_t)x * n + j]);
@@ -203,7 +199,7 @@ __global__ void k_power_sums(const cv<T> *fields, int n, DevCtl *ctl)
 
 // Signal spectrum in natural order: Sum |X_k|^2 and Sum k'|X_k|^2.
 template <class T>
-__global__ void k_spec_sums(const cv<T> *spec, int n, DevCtl *ctl)
+__device__ __forceinline__ void spec_body(const cv<T> *spec, int n, DevCtl *ctl)
 {
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
@@ -211,7 +207,7 @@ __global__ void k_spec_sums(const cv<T> *spec, int n, DevCtl *ctl)
         double p = (double)cabs2(spec[k]);
         int kk = (k < n / 2) ? k : k - n;
         s0 += p;
-        s1 += (double)kk * p;
+        s1 = __fma_rn((double)kk, p, s1);
     }
     s0 = block_sum(s0, red);
     s1 = block_sum(s1, red);
@@ -221,11 +217,11 @@ __global__ void k_spec_sums(const cv<T> *spec, int n, DevCtl *ctl)
     }
 }
 
+// Output-coupled fields (and their history row) of this round trip.
 template <class T>
-__global__ void k_save_output(const cv<T> *fields, cv<T> *out, int n, int F, T s0, T s1, T s2,
-                              cv<T> *hist, const DevCtl *ctl)
+__device__ __forceinline__ void save_body(const cv<T> *fields, cv<T> *out, int n, int F,
+                                          const T *sc, cv<T> *hist, const DevCtl *ctl)
 {
-    const T sc[3] = {s0, s1, s2};
     cv<T> *row = hist ? hist + (size_t)ctl->slot * F * n : nullptr; // history row of this round trip
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < F * n; i += gridDim.x * blockDim.x) {
         const cv<T> o = cscale(fields[i], sc[i / n]);
@@ -235,25 +231,19 @@ __global__ void k_save_output(const cv<T> *fields, cv<T> *out, int n, int F, T s
     }
 }
 
-struct CavArgs {
-    double bc_re[3], bc_im[3];
-    double eom_beta, eom_f, t_rt, dt;
-    unsigned resmask;
-    int eom;
-};
-
 // Mirror sqrt(R) e^{i delta} (Eq. (BC)) then the EOM phase (Sec. 2.3 item 2)
 // on resonant fields; the EOM argument frac(f_pm (tau_n + m t_rt)) is formed
 // in FP64.
 template <class T>
-__global__ void k_cavity_time(cv<T> *fields, int n, int F, CavArgs a, const DevCtl *ctl)
+__device__ __forceinline__ void cavity_body(cv<T> *fields, int n, int F, const PlainCav &a,
+                                            int64_t m)
 {
     using V = cv<T>;
-    const int64_t m = ctl->rt0 + ctl->slot;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         V mod = cmk<V>((T)1, (T)0);
         if (a.eom) {
-            double u = a.eom_f * ((double)(j - n / 2) * a.dt) + a.eom_f * ((double)m * a.t_rt);
+            const double u = __fma_rn(a.eom_f, (double)(j - n / 2) * a.dt,
+                                      a.eom_f * ((double)m * a.t_rt));
             double fr = u - floor(u);
             T ph;
             if constexpr (sizeof(T) == 8)
@@ -276,9 +266,257 @@ __global__ void k_cavity_time(cv<T> *fields, int n, int F, CavArgs a, const DevC
     }
 }
 
+// ------------------------------------------- single-instance kernels ----
+
+template <class T>
+__global__ void k_entry(cv<T> *fields, const cv<T> *pump, int n, int F, unsigned resmask,
+                        NsPump ns, const DevCtl *ctl)
+{
+    entry_body<T>(fields, pump, n, F, resmask, ns, ctl->rt0 + ctl->slot);
+}
+
+// Kerr coefficients G_xy (row-major) in the field precision.
+template <class T> struct KerrG {
+    T g[9];
+};
+
+template <class T>
+KerrG<T> kerr_g(const double *g)
+{
+    KerrG<T> k;
+    for (int i = 0; i < 9; i++)
+        k.g[i] = (T)g[i];
+    return k;
+}
+
+template <class T, int F>
+__global__ void k_rk4(cv<T> *fields, int n, const cv<T> *ekz, int q0, T h, T k0, T k1, T k2,
+                      bool use_e, bool kerr, KerrG<T> G)
+{
+    const T kap[3] = {k0, k1, k2};
+    rk4_body<T, F>(fields, n, ekz, q0, h, kap, use_e, kerr, G.g);
+}
+
+// grid (Q/B, fields)
+template <class T, int DIR>
+__global__ void k_fft_cols(const cv<T> *__restrict__ in, cv<T> *__restrict__ out, int n, int P,
+                           int Q, int logP, int logn, int B, const cv<T> *__restrict__ tw)
+{
+    fft_cols_body<T, DIR>(in + (size_t)blockIdx.y * n, out + (size_t)blockIdx.y * n, n, P, Q, logP,
+                          logn, B, tw, blockIdx.x);
+}
+
+// grid (P/B, fields)
+template <class T, int DIR>
+__global__ void k_fft_rows(const cv<T> *__restrict__ in, cv<T> *__restrict__ out, int n, int P,
+                           int Q, int logQ, int logn, int B, const cv<T> *__restrict__ tw)
+{
+    fft_rows_body<T, DIR>(in + (size_t)blockIdx.y * n, out + (size_t)blockIdx.y * n, n, P, Q, logQ,
+                          logn, B, tw, blockIdx.x);
+}
+
+template <class T>
+__global__ void k_mul_table(cv<T> *a, const cv<T> *__restrict__ tab, int total)
+{
+    mul_table_body<T>(a, tab, total);
+}
+
+// one block per field
+template <class T>
+__global__ void k_power_sums(const cv<T> *fields, int n, DevCtl *ctl)
+{
+    power_body<T>(fields, n, blockIdx.x, ctl);
+}
+
+template <class T>
+__global__ void k_spec_sums(const cv<T> *spec, int n, DevCtl *ctl)
+{
+    spec_body<T>(spec, n, ctl);
+}
+
+template <class T>
+__global__ void k_save_output(const cv<T> *fields, cv<T> *out, int n, int F, T s0, T s1, T s2,
+                              cv<T> *hist, const DevCtl *ctl)
+{
+    const T sc[3] = {s0, s1, s2};
+    save_body<T>(fields, out, n, F, sc, hist, ctl);
+}
+
+template <class T>
+__global__ void k_cavity_time(cv<T> *fields, int n, int F, PlainCav a, const DevCtl *ctl)
+{
+    cavity_body<T>(fields, n, F, a, ctl->rt0 + ctl->slot);
+}
+
 __global__ void k_end_rt(DevCtl *ctl)
 {
     ctl->slot += 1;
+}
+
+// --------------------------------------------------- batch kernels ----
+// Member blockIdx.z; the member's pointers and parameters come from its
+// descriptor.  Kernels of the cavity visit (mode argument of the transforms)
+// act on every field where the member's visit transforms every field
+// (spec_all), else on a copy of its signal in scratch slot 1.
+
+template <class T>
+__global__ void kb_entry(const PlainInst *__restrict__ insts, int n, int F)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    entry_body<T>((cv<T> *)I.fields, (const cv<T> *)I.pump, n, F, I.cav.resmask, I.ns,
+                  I.ctl->rt0 + I.ctl->slot);
+}
+
+template <class T, int F>
+__global__ void kb_rk4(const PlainInst *__restrict__ insts, int n, int kc, int q0)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    const CryDesc &cd = I.cry[kc];
+    const T kap[3] = {(T)cd.kappa[0], (T)cd.kappa[1], (T)cd.kappa[2]};
+    T G[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+        G[i] = (T)cd.kerr_g[i];
+    rk4_body<T, F>((cv<T> *)I.fields, n, (const cv<T> *)cd.ekz, q0, (T)cd.h, kap, cd.use_dk != 0,
+                   cd.kerr != 0, G);
+}
+
+// The buffer a transform of mode `mode` works on and its field count:
+// 0 the fields (all F); 1 the forward cavity visit (the fields, or the signal
+// copy); 2 the inverse cavity visit (the fields where spec_all, else none).
+template <class T>
+__device__ __forceinline__ cv<T> *visit_buffer(const PlainInst &I, int mode, int n, int F,
+                                               int *count)
+{
+    if (mode == 0 || (mode == 2 && I.spec_all)) {
+        *count = F;
+        return (cv<T> *)I.fields;
+    }
+    if (mode == 1) {
+        *count = I.spec_all ? F : 1;
+        return I.spec_all ? (cv<T> *)I.fields : (cv<T> *)I.scratch + n;
+    }
+    *count = 0;
+    return nullptr;
+}
+
+// grid (Q/B, F, members); the column pass writes scratch
+template <class T, int DIR>
+__global__ void kb_fft_cols(const PlainInst *__restrict__ insts, int mode, int n, int F, int P,
+                            int Q, int logP, int logn, int B)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    int count;
+    const cv<T> *a = visit_buffer<T>(I, mode, n, F, &count);
+    if ((int)blockIdx.y >= count)
+        return;
+    fft_cols_body<T, DIR>(a + (size_t)blockIdx.y * n, (cv<T> *)I.scratch + (size_t)blockIdx.y * n,
+                          n, P, Q, logP, logn, B, (const cv<T> *)I.tw, blockIdx.x);
+}
+
+// grid (P/B, F, members); the row pass reads scratch
+template <class T, int DIR>
+__global__ void kb_fft_rows(const PlainInst *__restrict__ insts, int mode, int n, int F, int P,
+                            int Q, int logQ, int logn, int B)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    int count;
+    cv<T> *a = visit_buffer<T>(I, mode, n, F, &count);
+    if ((int)blockIdx.y >= count)
+        return;
+    fft_rows_body<T, DIR>((const cv<T> *)I.scratch + (size_t)blockIdx.y * n, a + (size_t)blockIdx.y * n,
+                          n, P, Q, logQ, logn, B, (const cv<T> *)I.tw, blockIdx.x);
+}
+
+// kc >= 0: dispersion factors of crystal kc; kc < 0: the cavity spectral
+// factors (members whose visit transforms every field)
+template <class T>
+__global__ void kb_mul_table(const PlainInst *__restrict__ insts, int n, int F, int kc)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    if (kc < 0 && !I.spec_all)
+        return;
+    const cv<T> *tab = (const cv<T> *)(kc >= 0 ? I.cry[kc].disp : I.gdd);
+    mul_table_body<T>((cv<T> *)I.fields, tab, F * n);
+}
+
+// grid (F, 1, members)
+template <class T>
+__global__ void kb_power_sums(const PlainInst *__restrict__ insts, int n)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    power_body<T>((const cv<T> *)I.fields, n, blockIdx.x, I.ctl);
+}
+
+// the signal into scratch slot 1 where the visit transforms a copy
+template <class T>
+__global__ void kb_copy_signal(const PlainInst *__restrict__ insts, int n)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    if (I.spec_all)
+        return;
+    const cv<T> *src = (const cv<T> *)I.fields + n;
+    cv<T> *dst = (cv<T> *)I.scratch + n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        dst[j] = src[j];
+}
+
+template <class T>
+__global__ void kb_spec_sums(const PlainInst *__restrict__ insts, int n)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    const cv<T> *spec = I.spec_all ? (const cv<T> *)I.fields + n : (const cv<T> *)I.scratch + n;
+    spec_body<T>(spec, n, I.ctl);
+}
+
+template <class T>
+__global__ void kb_save_output(const PlainInst *__restrict__ insts, int n, int F)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    const T sc[3] = {(T)I.outscale[0], (T)I.outscale[1], (T)I.outscale[2]};
+    save_body<T>((const cv<T> *)I.fields, (cv<T> *)I.out, n, F, sc, (cv<T> *)I.hist, I.ctl);
+}
+
+template <class T>
+__global__ void kb_cavity_time(const PlainInst *__restrict__ insts, int n, int F)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    cavity_body<T>((cv<T> *)I.fields, n, F, I.cav, I.ctl->rt0 + I.ctl->slot);
+}
+
+__global__ void kb_end_rt(const PlainInst *__restrict__ insts, int count)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        insts[i].ctl->slot += 1;
+}
+
+__global__ void kb_begin(const PlainCall *__restrict__ calls, int count)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const PlainCall &c = calls[i];
+        c.ctl->rt0 = c.rt0;
+        c.ctl->slot = 0;
+        c.ctl->obs = c.obs;
+        c.ctl->parts = 1;
+    }
+}
+
+// The trace rows of every member (the arithmetic of the single-instance
+// finalize with one partial sum per round trip).
+__global__ void kb_finalize(const PlainCall *__restrict__ calls, int count, int64_t M)
+{
+    const int64_t total = (int64_t)count * M;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const PlainCall &c = calls[t / M];
+        const int64_t s = t % M;
+        double sum[kNslot] = {0, 0, 0, 0, 0};
+        for (int q = 0; q < kNslot; q++)
+            sum[q] += c.obs[s * kNslot + q];
+        for (int x = 0; x < 3; x++)
+            c.trace[s * 4 + x] = (x < c.F) ? sum[x] * c.inv_n * c.outscale2[x] * c.pscale[x] : 0.0;
+        c.trace[s * 4 + 3] = sum[3] > 0.0 ? (sum[4] / sum[3]) / c.t_window : 0.0;
+    }
 }
 
 int blocks_for(int64_t work)
@@ -287,15 +525,15 @@ int blocks_for(int64_t work)
     return (int)(b < 1 ? 1 : (b > 1184 ? 1184 : b));
 }
 
-template <class T>
-struct PlainFFT {
+// FFT plan of length N = P Q: column/row batch sizes and shared memory.
+struct FFTShape {
     int n, logn, P, Q, logP, logQ, Bc, Br;
     size_t smc, smr;
-    const cv<T> *tw;
-    void init(const opo_ctx *c)
+    template <class T>
+    void init(int n_)
     {
-        n = c->n;
-        logn = c->logn;
+        n = n_;
+        logn = ilog2((unsigned)n);
         logP = logn / 2;
         logQ = logn - logP;
         P = 1 << logP;
@@ -305,33 +543,57 @@ struct PlainFFT {
         Br = P < seg ? P : seg;
         smc = (size_t)2 * Bc * P * sizeof(cv<T>);
         smr = (size_t)2 * Br * (Q + 1) * sizeof(cv<T>);
-        tw = (const cv<T> *)c->d_tw;
     }
-    // the same plan for caller-given sizes and twiddle table
-    void init_raw(int n_, int logn_, const cv<T> *tw_)
+};
+
+template <class T>
+struct PlainFFT {
+    FFTShape sh;
+    const cv<T> *tw;
+    void init_raw(int n_, const cv<T> *tw_)
     {
-        n = n_;
-        logn = logn_;
-        logP = logn / 2;
-        logQ = logn - logP;
-        P = 1 << logP;
-        Q = 1 << logQ;
-        int seg = (sizeof(T) == 8) ? 4 : 8;
-        Bc = Q < seg ? Q : seg;
-        Br = P < seg ? P : seg;
-        smc = (size_t)2 * Bc * P * sizeof(cv<T>);
-        smr = (size_t)2 * Br * (Q + 1) * sizeof(cv<T>);
+        sh.template init<T>(n_);
         tw = tw_;
     }
     // transform `count` consecutive fields of `a` in place, scratch `s`
     template <int DIR>
     void run(cv<T> *a, cv<T> *s, int count, cudaStream_t st) const
     {
-        dim3 gc(Q / Bc, count), gr(P / Br, count);
-        k_fft_cols<T, DIR><<<gc, kThreads, smc, st>>>(a, s, n, P, Q, logP, logn, Bc, tw);
-        k_fft_rows<T, DIR><<<gr, kThreads, smr, st>>>(s, a, n, P, Q, logQ, logn, Br, tw);
+        dim3 gc(sh.Q / sh.Bc, count), gr(sh.P / sh.Br, count);
+        k_fft_cols<T, DIR><<<gc, kThreads, sh.smc, st>>>(a, s, sh.n, sh.P, sh.Q, sh.logP, sh.logn,
+                                                          sh.Bc, tw);
+        k_fft_rows<T, DIR><<<gr, kThreads, sh.smr, st>>>(s, a, sh.n, sh.P, sh.Q, sh.logQ, sh.logn,
+                                                          sh.Br, tw);
     }
 };
+
+PlainCav plain_cav(const opo_ctx *c)
+{
+    PlainCav ca;
+    for (int x = 0; x < 3; x++) {
+        ca.bc_re[x] = c->dv.bc_re[x];
+        ca.bc_im[x] = c->dv.bc_im[x];
+    }
+    ca.eom_beta = c->cavity.eom_beta_rad;
+    ca.eom_f = c->cavity.eom_f_hz;
+    ca.t_rt = c->cavity.t_rt_s > 0.0 ? c->cavity.t_rt_s : c->grid.t_window_s;
+    ca.dt = c->grid.t_window_s / (double)c->n;
+    ca.resmask = c->cavity.resonant_mask;
+    ca.eom = c->dv.eom ? 1 : 0;
+    return ca;
+}
+
+// The cavity visit transforms every field when a resonant field has GDD or
+// the timing mismatch is on; otherwise only a copy of the signal (for its
+// spectral centroid).
+bool spec_all_fields(const opo_ctx *c)
+{
+    for (int x = 0; x < c->F; x++)
+        if ((c->cavity.resonant_mask & (1u << x)) &&
+            (c->cavity.gdd_s2[x] != 0.0 || c->cavity.delay_s != 0.0))
+            return true;
+    return false;
+}
 
 template <class T>
 int enqueue_rt(opo_ctx *c, cudaStream_t st)
@@ -341,7 +603,7 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
     V *fld = (V *)c->d_fields;
     V *scr = (V *)c->d_scratch;
     PlainFFT<T> fft;
-    fft.init(c);
+    fft.init_raw(n, (const V *)c->d_tw);
     const Derived &d = c->dv;
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
     k_entry<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_pump, n, F, c->cavity.resonant_mask,
@@ -377,13 +639,8 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
                                                 (V *)c->d_hist, c->d_ctl);
     // cavity spectral visit: every resonant field with GDD or delay, and the
     // signal for its spectral centroid
-    bool need_all = false;
-    for (int x = 0; x < F; x++)
-        if ((c->cavity.resonant_mask & (1u << x)) &&
-            (c->cavity.gdd_s2[x] != 0.0 || c->cavity.delay_s != 0.0))
-            need_all = true;
     V *sig = fld + (size_t)n;
-    if (need_all) {
+    if (spec_all_fields(c)) {
         fft.template run<-1>(fld, scr, F, st);
         k_spec_sums<T><<<1, 1024, 0, st>>>(sig, n, c->d_ctl);
         k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_gdd, F * n);
@@ -395,19 +652,59 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
         fft.template run<-1>(copy, scr, 1, st);
         k_spec_sums<T><<<1, 1024, 0, st>>>(copy, n, c->d_ctl);
     }
-    CavArgs ca;
-    for (int x = 0; x < 3; x++) {
-        ca.bc_re[x] = d.bc_re[x];
-        ca.bc_im[x] = d.bc_im[x];
-    }
-    ca.eom_beta = c->cavity.eom_beta_rad;
-    ca.eom_f = c->cavity.eom_f_hz;
-    ca.t_rt = c->cavity.t_rt_s > 0.0 ? c->cavity.t_rt_s : c->grid.t_window_s;
-    ca.dt = c->grid.t_window_s / (double)n;
-    ca.resmask = c->cavity.resonant_mask;
-    ca.eom = d.eom ? 1 : 0;
-    k_cavity_time<T><<<gN, kThreads, 0, st>>>(fld, n, F, ca, c->d_ctl);
+    k_cavity_time<T><<<gN, kThreads, 0, st>>>(fld, n, F, plain_cav(c), c->d_ctl);
     k_end_rt<<<1, 1, 0, st>>>(c->d_ctl);
+    return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
+}
+
+// One round trip of every member of a batch, one launch per operation.
+template <class T>
+int enqueue_rt_batch(const opo_ctx *c0, const PlainInst *I, int count, cudaStream_t st)
+{
+    const int n = c0->n, F = c0->F;
+    FFTShape sh;
+    sh.template init<T>(n);
+    const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
+    auto fft = [&](int dir, int mode) {
+        dim3 gc(sh.Q / sh.Bc, F, count), gr(sh.P / sh.Br, F, count);
+        if (dir < 0) {
+            kb_fft_cols<T, -1><<<gc, kThreads, sh.smc, st>>>(I, mode, n, F, sh.P, sh.Q, sh.logP,
+                                                              sh.logn, sh.Bc);
+            kb_fft_rows<T, -1><<<gr, kThreads, sh.smr, st>>>(I, mode, n, F, sh.P, sh.Q, sh.logQ,
+                                                              sh.logn, sh.Br);
+        } else {
+            kb_fft_cols<T, 1><<<gc, kThreads, sh.smc, st>>>(I, mode, n, F, sh.P, sh.Q, sh.logP,
+                                                             sh.logn, sh.Bc);
+            kb_fft_rows<T, 1><<<gr, kThreads, sh.smr, st>>>(I, mode, n, F, sh.P, sh.Q, sh.logQ,
+                                                             sh.logn, sh.Br);
+        }
+    };
+    kb_entry<T><<<dim3(gFN, 1, count), kThreads, 0, st>>>(I, n, F);
+    for (int i = 0; i < c0->ncry; i++) {
+        for (int j = 0; j < c0->cry[i].nz; j++) {
+            for (int half = 0; half < 2; half++) {
+                const int q0 = 4 * j + 2 * half;
+                if (F == 3)
+                    kb_rk4<T, 3><<<dim3(gN, 1, count), kThreads, 0, st>>>(I, n, i, q0);
+                else
+                    kb_rk4<T, 2><<<dim3(gN, 1, count), kThreads, 0, st>>>(I, n, i, q0);
+                if (half == 0) {
+                    fft(-1, 0);
+                    kb_mul_table<T><<<dim3(gFN, 1, count), kThreads, 0, st>>>(I, n, F, i);
+                    fft(1, 0);
+                }
+            }
+        }
+    }
+    kb_power_sums<T><<<dim3(F, 1, count), 512, 0, st>>>(I, n);
+    kb_save_output<T><<<dim3(gFN, 1, count), kThreads, 0, st>>>(I, n, F);
+    kb_copy_signal<T><<<dim3(gN, 1, count), kThreads, 0, st>>>(I, n);
+    fft(-1, 1);
+    kb_spec_sums<T><<<dim3(1, 1, count), 1024, 0, st>>>(I, n);
+    kb_mul_table<T><<<dim3(gFN, 1, count), kThreads, 0, st>>>(I, n, F, -1);
+    fft(1, 2);
+    kb_cavity_time<T><<<dim3(gN, 1, count), kThreads, 0, st>>>(I, n, F);
+    kb_end_rt<<<(count + 255) / 256, 256, 0, st>>>(I, count);
     return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
 }
 
@@ -419,6 +716,10 @@ void prepare()
     cudaFuncSetAttribute(k_fft_cols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_fft_rows<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_fft_rows<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(kb_fft_cols<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(kb_fft_cols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(kb_fft_rows<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(kb_fft_rows<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 } // namespace
@@ -434,6 +735,68 @@ void plain_prepare(opo_ctx *c)
 int plain_enqueue_roundtrip(opo_ctx *c, cudaStream_t s)
 {
     return c->prec == OPO_FP64 ? enqueue_rt<double>(c, s) : enqueue_rt<float>(c, s);
+}
+
+void plain_fill_inst(PlainInst &p, const opo_ctx *c)
+{
+    p = PlainInst{};
+    p.fields = c->d_fields;
+    p.out = c->d_out;
+    p.scratch = c->d_scratch;
+    p.hist = c->d_hist;
+    p.pump = c->d_pump;
+    p.gdd = c->d_gdd;
+    p.tw = c->d_tw;
+    p.cry = c->d_cry;
+    p.ctl = c->d_ctl;
+    p.ns = c->dv.ns;
+    p.cav = plain_cav(c);
+    for (int x = 0; x < 3; x++)
+        p.outscale[x] = c->dv.outscale[x];
+    p.spec_all = spec_all_fields(c) ? 1 : 0;
+}
+
+void plain_fill_call(PlainCall &p, const opo_ctx *c)
+{
+    p = PlainCall{};
+    p.ctl = c->d_ctl;
+    p.obs = c->d_obs;
+    p.trace = c->d_trace;
+    p.rt0 = c->rt;
+    for (int x = 0; x < 3; x++) {
+        p.outscale2[x] = c->dv.outscale[x] * c->dv.outscale[x];
+        p.pscale[x] = c->dv.pscale[x];
+    }
+    p.inv_n = 1.0 / (double)c->n;
+    p.t_window = c->grid.t_window_s;
+    p.F = c->F;
+}
+
+int plain_batch_enqueue_roundtrip(const opo_ctx *c0, const PlainInst *d_insts, int count,
+                                  cudaStream_t s)
+{
+    if (c0->prec == OPO_FP64) {
+        prepare<double>();
+        return enqueue_rt_batch<double>(c0, d_insts, count, s);
+    }
+    prepare<float>();
+    return enqueue_rt_batch<float>(c0, d_insts, count, s);
+}
+
+int plain_batch_begin(const PlainCall *d_calls, int count, cudaStream_t s)
+{
+    kb_begin<<<(count + 255) / 256, 256, 0, s>>>(d_calls, count);
+    return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
+}
+
+int plain_batch_finalize(const PlainCall *d_calls, int count, int64_t M, cudaStream_t s)
+{
+    if (M <= 0)
+        return OPO_OK;
+    const int64_t work = (int64_t)count * M;
+    const int nb = (int)std::min<int64_t>((work + 255) / 256, 4096);
+    kb_finalize<<<nb, 256, 0, s>>>(d_calls, count, M);
+    return cudaGetLastError() == cudaSuccess ? OPO_OK : OPO_E_CUDA;
 }
 
 namespace {
@@ -452,7 +815,7 @@ int pass_raw(void *fields, void *scratch, const void *tw, const void *disp, cons
     V *fld = (V *)fields;
     V *scr = (V *)scratch;
     PlainFFT<T> fft;
-    fft.init_raw(n, ilog2((unsigned)n), (const V *)tw);
+    fft.init_raw(n, (const V *)tw);
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
     for (int j = 0; j < nz; j++) {
         for (int half = 0; half < 2; half++) {

@@ -10,11 +10,11 @@ Every tick the loop
    be resident at once (the library's occupancy query), a plain-path instance
    a fixed share; admission configures device state that then stays on the
    device until the request retires;
-3. advances every active instance by the same K round trips: all fused
-   instances in one batched launch (grouped by size class inside the
-   library), instances too large for the fused path on the plain path on their
-   own streams; the launches of newly admitted requests overlap with the work
-   of those already running;
+3. advances every active instance by the same K round trips in one batch:
+   fused instances grouped by size class inside the library, instances too
+   large for the fused path (or all of them, with ``path="plain"``) in
+   batched plain-path groups; the launches of newly admitted requests overlap
+   with the work of those already running;
 4. retires finished instances (output fields and trace copied to the host)
    and records latency = completion time - arrival time.
 
@@ -86,7 +86,10 @@ class Server:
     device bytes for instance state (default: half of the free memory).
     ``launch``: optional callable ``(n, nfields, precision) -> (cluster,
     threads, rt_per_launch)`` (e.g. from the autotuner); default shapes
-    otherwise.  Device state of retired requests is kept in a pool per
+    otherwise.  ``path="plain"`` runs every request on the batched plain
+    path (one kernel per operation) with the same admission shares the fused
+    path would get, so that the two forms are compared on the same trace.
+    Device state of retired requests is kept in a pool per
     (N, field count) and reconfigured for the next request of that class, so
     admission allocates only when a class needs more instances than ever
     before.  The loop is pipelined: while a tick runs on the GPU, arrivals
@@ -94,7 +97,7 @@ class Server:
     """
 
     def __init__(self, precision=opo.OPO_FP32_PH64, device=0, tick_rt=16, gpu_share=1.0,
-                 hbm_budget=None, launch=None, plain_share=0.1):
+                 hbm_budget=None, launch=None, plain_share=0.1, path="auto"):
         import torch
         self.precision = precision
         self.device = device
@@ -106,6 +109,9 @@ class Server:
         self.hbm_budget = int(hbm_budget)
         self.launch = launch
         self.plain_share = float(plain_share)
+        if path not in ("auto", "plain"):
+            raise ValueError("path is 'auto' or 'plain'")
+        self.path = path
         self.capacity = {}  # (n, F, cluster, threads) -> resident clusters
         self.results = []
         self.ticks = 0
@@ -153,8 +159,11 @@ class Server:
             share = 1.0 / max(1, cap)
         except opo.OPOError:
             path, cluster = opo.OPO_PATH_PLAIN, 0
-            ctx.set_path(opo.OPO_PATH_PLAIN)
             share = self.plain_share
+        if self.path == "plain":
+            path, cluster = opo.OPO_PATH_PLAIN, 0
+        if path == opo.OPO_PATH_PLAIN:
+            ctx.set_path(opo.OPO_PATH_PLAIN)
         if share_used + share > self.gpu_share + 1e-9 and share_used > 0:
             self._release(ctx, cfg)
             return None
@@ -214,10 +223,7 @@ class Server:
             groups = collections.defaultdict(list)
             for a in active:
                 a.k = min(self.tick_rt, a.req.rounds - a.done)
-                if a.path == opo.OPO_PATH_FUSED:
-                    groups[a.k].append(a)
-                else:
-                    opo.opo_run_roundtrips(a.ctx.h, a.k)
+                groups[a.k].append(a)
             live = set()
             for k, members in groups.items():
                 key = (k, tuple(id(a) for a in members))

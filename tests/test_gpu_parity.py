@@ -543,6 +543,10 @@ LARGE_CASES = [
      opo.OPO_FP64, opo.OPO_PATH_AUTO),
     ("plain_n131072_degenerate_dk", lambda: cfg_degenerate(n=1 << 17).replace(nz=3),
      opo.OPO_FP32_PH64, opo.OPO_PATH_PLAIN),
+    ("plain_n131072_sync_eom", lambda: W.sync_pumped_64k(delay_fs=-5.0).replace(n=1 << 17, nz=2),
+     opo.OPO_FP32_PH64, opo.OPO_PATH_PLAIN),
+    ("plain_n65536_sync_eom", lambda: W.sync_pumped_64k(delay_fs=7.0).replace(nz=2),
+     opo.OPO_FP64, opo.OPO_PATH_PLAIN),
     ("plain_n65536_dro_loss_dk", lambda: cfg_dro(n=1 << 16).replace(nz=3), opo.OPO_FP32_PH64,
      opo.OPO_PATH_PLAIN),
 ]
@@ -561,3 +565,66 @@ def test_large_n_round_trip(name, make, prec, path):
     compare(cfg, got, ref, prec, name, test="large_n")
     if path != opo.OPO_PATH_AUTO:
         assert got[3].path == path
+
+
+# ----- three FP32 fields at 2^17 and FP64 at 2^16: fused, one 16-CTA cluster
+# per instance holding N/16 points per field once, the exchange between CTAs
+# through two L2-resident global buffers
+
+XG_CASES = [
+    ("sync_eom_delay_n131072", lambda: W.sync_pumped_64k(delay_fs=-15.0).replace(n=1 << 17, nz=3),
+     opo.OPO_FP32_PH64),
+    ("degenerate_dk_n131072", lambda: cfg_degenerate(n=1 << 17).replace(nz=3), opo.OPO_FP32_PH64),
+    ("dro_loss_dk_n131072", lambda: cfg_dro(n=1 << 17).replace(nz=2), opo.OPO_FP32_PH64),
+    ("sync_eom_delay_n65536", lambda: W.sync_pumped_64k(delay_fs=12.0).replace(nz=3),
+     opo.OPO_FP64),
+    ("degenerate_dk_n65536", lambda: cfg_degenerate(n=1 << 16).replace(nz=3), opo.OPO_FP64),
+    ("kerr_n65536", lambda: cfg_dispersive(n=1 << 16, nz=2).replace(n2=2e-17, dk=40.0,
+                                                                    beta4=(4e-55, 0.0, 2e-55)),
+     opo.OPO_FP64),
+    ("kerr_n131072", lambda: cfg_dispersive(n=1 << 17, nz=2).replace(n2=2e-17, dk=40.0,
+                                                                     beta4=(4e-55, 0.0, 2e-55)),
+     opo.OPO_FP32_PH64),
+]
+
+
+@pytest.mark.parametrize("name,make,prec", XG_CASES, ids=[c[0] for c in XG_CASES])
+def test_fused_global_exchange_round_trip(name, make, prec):
+    """One round trip on the fused form that exchanges through global memory,
+    element by element against the oracle."""
+    cfg = make()
+    a0 = strong(cfg, 1e6)
+    ref = oracle_rt(cfg, a0, m0=2)
+    got = gpu_rt(cfg, a0, prec, opo.OPO_PATH_FUSED, m0=2)
+    compare(cfg, got, ref, prec, name, test="global_exchange")
+    assert got[3].path == opo.OPO_PATH_FUSED and got[3].cluster == 16
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=["fp64", "fp32ph64"])
+def test_fused_global_exchange_batch_resume_bitwise(prec):
+    """Several round trips per launch, a batch of two, and a resume: bit for
+    bit the lone run (2^16 in FP64, 2^17 in FP32)."""
+    n = 1 << 16 if prec == opo.OPO_FP64 else 1 << 17
+    base = W.sync_pumped_64k(delay_fs=-10.0).replace(n=n, nz=2)
+    cfgs = [base, base.replace(pump_power=1.5 * base.pump_power, delay=5e-15)]
+    starts = [strong(c, 1e6, i) for i, c in enumerate(cfgs)]
+    alone = []
+    for c, a in zip(cfgs, starts):
+        with opo.Context(c, precision=prec, fields=a) as ctx:
+            ctx.set_path(opo.OPO_PATH_FUSED, 16, 2)
+            ctx.run(3)
+            alone.append((ctx.get_fields(), ctx.trace(3)))
+    ctxs = [opo.Context(c, precision=prec, fields=a) for c, a in zip(cfgs, starts)]
+    try:
+        for c in ctxs:
+            c.set_path(opo.OPO_PATH_FUSED, 16, 2)
+        b = opo.opo_batch_create([c.h for c in ctxs], 0, 0)
+        opo.opo_batch_run(b, 1)
+        opo.opo_batch_run(b, 2)
+        for ctx, (f, t) in zip(ctxs, alone):
+            assert np.array_equal(ctx.get_fields(), f)
+            assert np.array_equal(ctx.trace(2), t[1:])
+        opo.opo_batch_destroy(b)
+    finally:
+        for c in ctxs:
+            c.close()

@@ -26,21 +26,28 @@ def _requests():
         (mk(16384, pump_kind=W.PUMP_SECH2, pump_fwhm=1e-12, eom_beta=0.5, eom_f=10e9,
             delay=10e-15), 17, 0.02),
         (mk(4096, instance=7, pump_power=2 * base.pump_power), 50, 0.05),
-        (mk(131072), 4, 0.06),  # too large for the fused path: plain path
+        # fused with the exchange through global memory in FP32; too large
+        # for the fused path in FP64 (plain path)
+        (mk(131072), 4, 0.06),
     ]
     return [serving.Request(i, c.replace(instance=i), m, t) for i, (c, m, t) in enumerate(cfgs)]
 
 
-def test_results_do_not_depend_on_the_mix():
+@pytest.mark.parametrize("prec,mode", [(opo.OPO_FP32_PH64, "auto"), (opo.OPO_FP64, "auto"),
+                                       (opo.OPO_FP32_PH64, "plain")],
+                         ids=["fp32-auto", "fp64-auto", "fp32-plain"])
+def test_results_do_not_depend_on_the_mix(prec, mode):
     reqs = _requests()
-    srv = serving.Server(tick_rt=8)
+    srv = serving.Server(precision=prec, tick_rt=8, path=mode)
     res = {r.rid: r for r in srv.run(reqs)}
     assert sorted(res) == [r.rid for r in reqs]
     assert srv.ticks >= 5
     paths = set()
     for req in reqs:
-        with opo.Context(req.cfg) as ctx:
+        with opo.Context(req.cfg, precision=prec) as ctx:
             try:
+                if mode == "plain":
+                    raise opo.OPOError(opo.OPO_E_UNSUPPORTED, "plain requested")
                 ctx.set_path(opo.OPO_PATH_FUSED)
                 path = opo.OPO_PATH_FUSED
             except opo.OPOError:
@@ -56,7 +63,9 @@ def test_results_do_not_depend_on_the_mix():
         assert np.array_equal(got.out_fields, alone_out), req.rid
         # the trace of a lone call covers all rounds; the server's is per tick
         assert np.array_equal(got.trace, alone_tr), req.rid
-    assert paths == {opo.OPO_PATH_FUSED, opo.OPO_PATH_PLAIN}
+    want = {"auto": {opo.OPO_PATH_FUSED} if prec == opo.OPO_FP32_PH64 else
+            {opo.OPO_PATH_FUSED, opo.OPO_PATH_PLAIN}, "plain": {opo.OPO_PATH_PLAIN}}[mode]
+    assert paths == want
 
 
 def test_admission_respects_budgets():

@@ -96,3 +96,47 @@ def test_steady_state_power_and_centroid(name, path, prec):
     if name == "sro_off_carrier":
         # the steady state sits far off the carrier compared with the tolerance
         assert abs(nu_ref) > 100 * tol * max(width, floor)
+
+
+# ----------------------------------------------- the 2^14-point workload
+# The stored oracle run (tests/golden/steady_state_cw_sro_16k.json, written by
+# tests/golden/make_steady_state.py from oracle/ only): the 2^14-point CW SRO
+# with GVM, GVD, TOD and intracavity GDD at 4x threshold, from the seeded
+# 1e-15 V/m noise through growth, saturation and relaxation to steady state.
+
+import json  # noqa: E402
+import os  # noqa: E402
+
+GOLDEN_16K = os.path.join(os.path.dirname(__file__), "golden", "steady_state_cw_sro_16k.json")
+TOL_16K = {opo.OPO_FP64: 1e-6, opo.OPO_FP32_PH64: 1e-3}
+
+
+@pytest.mark.parametrize("prec,path", [(opo.OPO_FP32_PH64, opo.OPO_PATH_FUSED),
+                                       (opo.OPO_FP32_PH64, opo.OPO_PATH_PLAIN),
+                                       (opo.OPO_FP64, opo.OPO_PATH_FUSED)],
+                         ids=["fp32ph64-fused", "fp32ph64-plain", "fp64-fused"])
+def test_steady_state_n16384_from_noise(prec, path):
+    """Same start (the seeded noise), same number of round trips as the
+    oracle run; the means of P_s,out and of the signal centroid over the last
+    K round trips agree within 1e-3 (FP32 fields, FP64 phases) and 1e-6
+    (FP64), the centroid in units of the output's rms spectral width (floored
+    at half a frequency bin)."""
+    ref = json.load(open(GOLDEN_16K))
+    cfg = W.cw_sro_16k()
+    assert ref["workload"] == cfg.name
+    M, K = ref["rt"], ref["last"]
+    with opo.Context(cfg, precision=prec) as ctx:
+        ctx.set_path(path)
+        ctx.run(M)
+        tr = ctx.trace(M)
+    tol = TOL_16K[prec]
+    ps = tr[-K:, 1].mean()
+    ps_ref = ref["p_out_mean_W"][1]
+    assert abs(ps - ps_ref) <= tol * ps_ref, (ps, ps_ref)
+    nu = tr[-K:, 3].mean()
+    scale = max(ref["width_hz"], 0.5 / cfg.t_window)
+    assert abs(nu - ref["centroid_mean_hz"]) <= tol * scale, (nu, ref["centroid_mean_hz"], scale)
+    # the pump is depleted as the oracle says (same tolerance, in units of
+    # the input pump power)
+    pp = tr[-K:, 0].mean()
+    assert abs(pp - ref["p_out_mean_W"][0]) <= tol * cfg.pump_power, (pp, ref["p_out_mean_W"][0])

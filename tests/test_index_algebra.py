@@ -26,7 +26,7 @@ re-derive each access both ways and compare them element by element.
 import numpy as np
 import pytest
 
-SIZES = [(6, 6), (6, 7), (7, 7), (7, 8), (8, 8)]
+SIZES = [(6, 6), (6, 7), (7, 7), (7, 8), (8, 8), (8, 9)]
 
 
 def col_split(LP):
@@ -35,13 +35,18 @@ def col_split(LP):
     return LP - A2, A2
 
 
+def row_split(LQ):
+    """[Rb1, Rb2] exponents of the row transform (Q = 512 splits [32, 16])."""
+    B2 = 4 if LQ == 9 else (LQ + 1) // 2
+    return LQ - B2, B2
+
+
 def layout(LP, LQ, dbl, C, F):
     S = 16 if dbl else 8            # bytes per complex element
     SW = 3 if dbl else 4            # 128-byte bank row = 2^SW elements
     SWM = (1 << SW) - 1
     A1, A2 = col_split(LP)
-    B2 = (LQ + 1) // 2
-    B1 = LQ - B2
+    B1, B2 = row_split(LQ)
     N = 1 << (LP + LQ)
     NC = N // C
     logC = C.bit_length() - 1
@@ -176,3 +181,53 @@ def test_a_plausible_slip_is_caught():
     want = g["Yoff"] + S * g["ridx"](0, (1 + r * Ra1) & (Pc - 1), n2)
     assert np.array_equal(base + (a0 ^ (S * perm(R))), want)
     assert not np.array_equal(base + a0, want)
+
+
+@pytest.mark.parametrize("LP,LQ,dbl", [(8, 9, False), (8, 8, True)])
+@pytest.mark.parametrize("F", [2, 3])
+def test_global_exchange_covers_every_element_once(LP, LQ, dbl, F):
+    """The form that exchanges through global memory (three FP32 fields at
+    2^17, FP64 at 2^16; 16 CTAs): the forward push and the inverse push each
+    write every element of their buffer exactly once, the row stage and the
+    column stage after the barriers read every element exactly once, and each
+    CTA's reads fill its whole in-place buffer (Y, then X) exactly once."""
+    C = 16
+    g = layout(LP, LQ, dbl, C, F)
+    Ra1, Ra2, Rb1, Rb2 = g["Ra1"], g["Ra2"], g["Rb1"], g["Rb2"]
+    Pc, Qc, logPc, logQc = g["Pc"], g["Qc"], g["logPc"], g["logQc"]
+    P, Q = 1 << LP, 1 << LQ
+    N = P * Q
+    c = np.arange(C)[:, None, None, None, None]
+    f = np.arange(F)[None, :, None, None, None]
+    # forward push: column b of CTA c, butterfly j < Ra1, output r < Ra2 ->
+    # G1[f][k1 = j + r Ra1][n2 = c Qc + b]
+    b = np.arange(Qc)[None, None, :, None, None]
+    j = np.arange(Ra1)[None, None, None, :, None]
+    r = np.arange(Ra2)[None, None, None, None, :]
+    w1 = (f * N + (j + r * Ra1) * Q + (c << logQc) + b).ravel()
+    assert np.array_equal(np.sort(w1), np.arange(F * N))
+    # row stage: CTA c, row < Pc, butterfly j < Rb2, input r < Rb1 reads
+    # G1[f][c Pc + row][j + r Rb2] and writes Y element j Rb1 + r of that row
+    row = np.arange(Pc)[None, None, :, None, None]
+    j = np.arange(Rb2)[None, None, None, :, None]
+    r = np.arange(Rb1)[None, None, None, None, :]
+    r1 = (f * N + ((c << logPc) + row) * Q + j + r * Rb2).ravel()
+    assert np.array_equal(np.sort(r1), np.arange(F * N))
+    ya = np.broadcast_to(g["ridx"](f, row, j * Rb1 + r), (C, F, Pc, Rb2, Rb1))
+    for cc in range(C):
+        assert np.array_equal(np.sort(ya[cc].ravel()), np.arange(F * g["NC"]))
+    # inverse push: CTA c, row < Pc, butterfly j < Rb2, output r < Rb1 ->
+    # G2[f][n1 = c Pc + row][n2 = j + r Rb2]
+    w2 = (f * N + ((c << logPc) + row) * Q + j + r * Rb2).ravel()
+    assert np.array_equal(np.sort(w2), np.arange(F * N))
+    # column stage: CTA c, column b < Qc, butterfly j < Ra1, input r < Ra2
+    # reads G2[f][j + r Ra1][c Qc + b] and writes X element j Ra2 + r of
+    # column b
+    b = np.arange(Qc)[None, None, :, None, None]
+    j = np.arange(Ra1)[None, None, None, :, None]
+    r = np.arange(Ra2)[None, None, None, None, :]
+    r2 = (f * N + (j + r * Ra1) * Q + (c << logQc) + b).ravel()
+    assert np.array_equal(np.sort(r2), np.arange(F * N))
+    xa = np.broadcast_to(g["cidx"](f, j * Ra2 + r, b), (C, F, Qc, Ra1, Ra2))
+    for cc in range(C):
+        assert np.array_equal(np.sort(xa[cc].ravel()), np.arange(F * g["NC"]))
