@@ -305,6 +305,20 @@ OPO_API const char *opo_status_string(int status);
 OPO_API int opo_batch_create(opo_batch **out, opo_ctx *const *ctxs, int32_t count, int32_t cluster,
                              int32_t threads);
 OPO_API int opo_batch_run(opo_batch *batch, int64_t m);
+
+/* on = 1: run every fused member of the batch in one persistent launch (the
+ * batched sweep of mixed sizes as a single kernel launch): one cluster size
+ * and CTA size for all, those that hold the largest member, and the generic
+ * fused kernel when sizes or field counts differ (it takes N, F and every
+ * parameter per instance from its descriptor).  The launch configuration
+ * then follows the largest member, so a member's rounding may depend on the
+ * mix (and differ from its lone run, which uses its size class's own
+ * kernel); results stay within the stated tolerances of the oracle.  on = 0:
+ * one launch per size class again (the default: each class keeps its own
+ * kernel, cluster and CTA size, and every member advances bit for bit as it
+ * would alone).  Plain-path members are not affected.  OPO_E_UNSUPPORTED if
+ * no single configuration holds every fused member.  Waits for the device. */
+OPO_API int opo_batch_set_one_launch(opo_batch *batch, int32_t on);
 OPO_API int opo_batch_destroy(opo_batch *batch);
 
 /* Host transfers of a whole batch (one copy each way instead of one per field

@@ -921,6 +921,7 @@ struct opo_batch {
     std::vector<opo_ctx *> ctxs;
     std::vector<BatchGroup> groups;
     cudaStream_t capture = nullptr; // capture of the plain groups' graphs
+    bool one_launch = false;        // all fused members in one launch
     std::vector<cudaEvent_t> ev; // one per context: stream ordering
     cudaEvent_t fork = nullptr;
     int device = 0;              // copies, so that destroying the batch never
@@ -1187,7 +1188,9 @@ int batch_check_err(opo_batch *b)
 
 // A member's state no longer matches the group it was put in (its crystals
 // or path request changed after the batch was made).
-bool group_stale(const BatchGroup &gg)
+// In one-launch mode a fused group runs the union of its members' nonlinear
+// variants (a member may then sit in a more general kernel than alone).
+bool group_stale(const BatchGroup &gg, bool one_launch)
 {
     for (const opo_ctx *c : gg.ctxs) {
         if (gg.plain) {
@@ -1196,7 +1199,14 @@ bool group_stale(const BatchGroup &gg)
             for (int k = 0; k < c->ncry; k++)
                 if (c->cry[k].nz != gg.nzs[k])
                     return true;
-        } else if (c->path_req == OPO_PATH_PLAIN || nl_variant(c) != gg.cfg.nl) {
+        } else if (c->path_req == OPO_PATH_PLAIN) {
+            return true;
+        } else if (one_launch) {
+            const int v = nl_variant(c);
+            if (gg.cfg.kernel >= 2 && v != gg.cfg.nl && gg.cfg.nl != kNlKerr &&
+                !(gg.cfg.nl == kNlChi2 && v == kNlChi2NoDk))
+                return true;
+        } else if (nl_variant(c) != gg.cfg.nl) {
             return true;
         }
     }
@@ -1361,7 +1371,7 @@ int opo_batch_run(opo_batch *b, int64_t m)
     cudaStream_t s = c0->stream;
     const int count = (int)b->ctxs.size();
     for (const BatchGroup &gg : b->groups) {
-        if (group_stale(gg))
+        if (group_stale(gg, b->one_launch))
             return OPO_E_STATE;
         for (opo_ctx *c : gg.ctxs) {
             int rc = begin_call(c, m, gg.plain ? 1 : gg.cfg.cluster, false);
@@ -1411,6 +1421,101 @@ int opo_batch_run(opo_batch *b, int64_t m)
             cudaStreamWaitEvent(c->stream, b->ev[i], 0);
         }
     }
+    return rc;
+}
+
+int opo_batch_set_one_launch(opo_batch *b, int32_t on)
+{
+    if (!b || (on != 0 && on != 1))
+        return OPO_E_INVALID;
+    DeviceGuard g(b->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    cudaDeviceSynchronize(); // the groups' streams and graphs may be in use
+    // the fused members, in batch order
+    std::vector<opo_ctx *> fused;
+    std::vector<BatchGroup> plain;
+    for (BatchGroup &gg : b->groups) {
+        if (gg.plain) {
+            plain.push_back(gg);
+            gg.d_insts = nullptr; // moved
+            gg.d_calls = nullptr;
+            gg.graph = nullptr;
+        }
+    }
+    for (opo_ctx *c : b->ctxs)
+        for (const BatchGroup &gg : b->groups)
+            if (!gg.plain && std::find(gg.ctxs.begin(), gg.ctxs.end(), c) != gg.ctxs.end())
+                fused.push_back(c);
+    std::vector<BatchGroup> groups;
+    if (!fused.empty()) {
+        if (on) {
+            // one launch: a configuration holding every fused member (the
+            // generic kernel when sizes or field counts differ)
+            int fmin = 3, fmax = 2, nmin = 1 << 17, nmax = 16, rtpl = 0;
+            bool kerr = false, dk = false;
+            for (const opo_ctx *c : fused) {
+                fmin = std::min(fmin, c->F);
+                fmax = std::max(fmax, c->F);
+                nmin = std::min(nmin, c->n);
+                nmax = std::max(nmax, c->n);
+                rtpl = std::max(rtpl, c->rtpl_req);
+                kerr = kerr || c->kerr_any;
+                dk = dk || c->dk_any;
+            }
+            BatchGroup gg;
+            gg.ctxs = fused;
+            const int nl = kerr ? kNlKerr : (dk ? kNlChi2 : kNlChi2NoDk);
+            if (!fused_config(fused[0]->csz, fmin, fmax, nmin, nmax, 0, rtpl, 0, nl, &gg.cfg))
+                return OPO_E_UNSUPPORTED;
+            groups.push_back(gg);
+        } else {
+            // back to one launch per size class: rebuild the batch's groups
+            opo_batch *t = nullptr;
+            int rc = opo_batch_create(&t, fused.data(), (int)fused.size(), 0, 0);
+            if (rc != OPO_OK)
+                return rc;
+            for (BatchGroup &gg : t->groups)
+                if (!gg.plain) {
+                    BatchGroup x;
+                    x.ctxs = gg.ctxs;
+                    x.cfg = gg.cfg;
+                    groups.push_back(x);
+                }
+            opo_batch_destroy(t);
+        }
+    }
+    for (BatchGroup &gg : b->groups) {
+        if (gg.stream)
+            cudaStreamDestroy(gg.stream);
+        if (gg.done)
+            cudaEventDestroy(gg.done);
+        if (gg.graph)
+            cudaGraphExecDestroy(gg.graph);
+        if (gg.d_insts)
+            cudaFree(gg.d_insts);
+        if (gg.d_calls)
+            cudaFree(gg.d_calls);
+    }
+    for (BatchGroup &gg : plain)
+        groups.push_back(gg);
+    b->groups = groups;
+    int rc = OPO_OK;
+    if (b->groups.size() > 1)
+        for (BatchGroup &gg : b->groups) {
+            gg.stream = nullptr;
+            gg.done = nullptr;
+            if (rc == OPO_OK)
+                rc = cuda_status(cudaStreamCreateWithFlags(&gg.stream, cudaStreamNonBlocking));
+            if (rc == OPO_OK)
+                rc = cuda_status(cudaEventCreateWithFlags(&gg.done, cudaEventDisableTiming));
+        }
+    else
+        for (BatchGroup &gg : b->groups) {
+            gg.stream = nullptr;
+            gg.done = nullptr;
+        }
+    b->one_launch = on != 0;
     return rc;
 }
 

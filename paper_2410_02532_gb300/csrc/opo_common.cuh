@@ -185,6 +185,16 @@ __device__ __forceinline__ V add_ig(V y, typename cscal<V>::type g, V p)
     return cmk<V>(fmad_(-g, p.y, y.x), fmad_(g, p.x, y.y));
 }
 
+// p1 + 2 p2 + 2 p3 + p4, evaluated left to right (the doublings are exact)
+template <class V>
+__device__ __forceinline__ V rk4_sum(V p1, V p2, V p3, V p4)
+{
+    using S = typename cscal<V>::type;
+    S sx = p1.x + (S)2 * p2.x + (S)2 * p3.x + p4.x;
+    S sy = p1.y + (S)2 * p2.y + (S)2 * p3.y + p4.y;
+    return cmk<V>(sx, sy);
+}
+
 template <int F, int EM, class V>
 __device__ __forceinline__ void rk4_point_e(V *y, V e0, V e1, V e2,
                                             const typename cscal<V>::type *kap,
@@ -214,11 +224,8 @@ __device__ __forceinline__ void rk4_point_e(V *y, V e0, V e1, V e2,
         t[x] = add_ig(y[x], c[x], p3[x]);
     nl_prod<F, EM>(t, e2, use_e, p4);
 #pragma unroll
-    for (int x = 0; x < F; x++) {
-        S sx = p1[x].x + (S)2 * p2[x].x + (S)2 * p3[x].x + p4[x].x;
-        S sy = p1[x].y + (S)2 * p2[x].y + (S)2 * p3[x].y + p4[x].y;
-        y[x] = add_ig(y[x], c6[x], cmk<V>(sx, sy));
-    }
+    for (int x = 0; x < F; x++)
+        y[x] = add_ig(y[x], c6[x], rk4_sum(p1[x], p2[x], p3[x], p4[x]));
 }
 
 // RK4 step of the same system with the Kerr (chi(3)) terms added:
@@ -268,11 +275,8 @@ __device__ __forceinline__ void rk4_point_kerr_e(V *y, V e0, V e1, V e2,
         t[x] = add_ig(y[x], h, q3[x]);
     rhs(t, e2, q4);
 #pragma unroll
-    for (int x = 0; x < F; x++) {
-        S sx = q1[x].x + (S)2 * q2[x].x + (S)2 * q3[x].x + q4[x].x;
-        S sy = q1[x].y + (S)2 * q2[x].y + (S)2 * q3[x].y + q4[x].y;
-        y[x] = add_ig(y[x], h6, cmk<V>(sx, sy));
-    }
+    for (int x = 0; x < F; x++)
+        y[x] = add_ig(y[x], h6, rk4_sum(q1[x], q2[x], q3[x], q4[x]));
 }
 
 template <int F, class V>

@@ -6,11 +6,14 @@
 //   mirror + EOM | round-trip counter
 // and is captured once into a CUDA graph that every round trip replays.
 //
-// The FFT of length N = P Q runs as two kernels (four-step decomposition,
-// n = Q n1 + n2, k = k1 + P k2): P-point column transforms with the twiddle
-// W_N^{n2 k1} written to scratch, then Q-point row transforms written back in
-// natural order.  Each kernel transforms a batch of columns or rows in shared
-// memory with Stockham stages of radix 2..16.
+// An FFT of a field that fits one CTA's shared memory (2^8 <= N <= 2^14 in
+// FP32, 2^13 in FP64; N/16 threads) is one kernel: the field is loaded once, every
+// Stockham stage (radix 2..8) runs in place in shared memory, and it is
+// stored once.  Larger fields (N = P Q) take two kernels (four-step
+// decomposition, n = Q n1 + n2, k = k1 + P k2): P-point column transforms
+// with the twiddle W_N^{n2 k1} written to scratch, then Q-point row
+// transforms written back in natural order, each kernel transforming a batch
+// of columns or rows in shared memory.
 //
 // Two launch forms share every kernel body: one instance per launch (a
 // context's own graph; the allocation-free pass), and a batch in which each
@@ -154,6 +157,90 @@ __device__ __forceinline__ void fft_rows_body(const cv<T> *__restrict__ src, cv<
         int b = i % B, k2 = i / B;
         dst[(size_t)(k1b + b) + (size_t)P * k2] = a[b * Lp + k2];
     }
+}
+
+// Whole-field transforms: VPT = 16 values per thread, so N/16 threads; the field sits in shared memory with one pad element after
+// every 16 (index i at i + i/16), which spreads the stride-R stores of the
+// early stages over the banks.
+template <class T> constexpr int kFieldVpt = 16;
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+
+// One radix-R Stockham stage over the whole field in place: each thread
+// takes VPT/R butterflies, loads all their inputs into registers, waits at a
+// barrier for every other thread to do the same, then stores its outputs
+// over the same buffer.  Butterfly j reads s[j + r N/R], multiplies by
+// W_{Ns R}^{DIR r k} (k = j mod Ns), takes an R-point DFT and stores output r
+// at (j - k) R + k + r Ns.
+template <int R, int VPT, int DIR, class V>
+__device__ __forceinline__ void field_stage(V *s, int n, int Ns, const V *__restrict__ tw,
+                                            int twshift)
+{
+    constexpr int B = VPT / R; // butterflies per thread
+    const int Lr = n / R;
+    V v[B][R];
+#pragma unroll
+    for (int q = 0; q < B; q++) {
+        const int j = threadIdx.x + q * blockDim.x;
+        const int k = j & (Ns - 1);
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            v[q][r] = s[fpad(j + r * Lr)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                V w = tw[(r * k) << twshift];
+                if (DIR > 0)
+                    w.y = -w.y;
+                v[q][r] = cmul(v[q][r], w);
+            }
+        }
+        dft<R, DIR>(v[q]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < B; q++) {
+        const int j = threadIdx.x + q * blockDim.x;
+        const int k = j & (Ns - 1);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            s[fpad(base + r * Ns)] = v[q][r];
+    }
+    __syncthreads();
+}
+
+// Whole-field transform of one field (N <= 2^14 in FP32, 2^13 in FP64: the
+// field fits one CTA's shared memory): one load and one store of the field,
+// every Stockham stage in shared memory in between.  blockDim = N/VPT.
+template <class T, int DIR>
+__device__ __forceinline__ void fft_field_body(cv<T> *a, int n, int logn,
+                                               const cv<T> *__restrict__ tw)
+{
+    using V = cv<T>;
+    constexpr int VPT = kFieldVpt<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *s = reinterpret_cast<V *>(smem_raw);
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        s[fpad(i)] = a[i];
+    __syncthreads();
+    // stages of radix at most 8 (a radix-16 DFT and its temporaries do not
+    // fit the 64 registers of 1024 threads), the log2 N bits split as evenly
+    // as possible, largest first
+    const int nst = (logn + 2) / 3;
+    int Ns = 1, lg = 0;
+    for (int st = 0; st < nst; st++) {
+        const int lr = logn / nst + (st < logn % nst ? 1 : 0);
+        const int shift = logn - (lg + lr); // tw holds W_N^i: W_{Ns R} = W_N^{N/(Ns R)}
+        switch (lr) {
+        case 1: field_stage<2, VPT, DIR>(s, n, Ns, tw, shift); break;
+        case 2: field_stage<4, VPT, DIR>(s, n, Ns, tw, shift); break;
+        default: field_stage<8, VPT, DIR>(s, n, Ns, tw, shift); break;
+        }
+        Ns <<= lr;
+        lg += lr;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        a[i] = s[fpad(i)];
 }
 
 template <class T>
@@ -315,6 +402,18 @@ __global__ void k_fft_rows(const cv<T> *__restrict__ in, cv<T> *__restrict__ out
                           logn, B, tw, blockIdx.x);
 }
 
+// threads of a whole-field transform: N/16, at most 2^14/16 (FP32) and
+// 2^13/16 (FP64)
+template <class T> constexpr int kFieldThreads = sizeof(T) == 8 ? 512 : 1024;
+
+// grid (fields): one whole-field transform per CTA, in place
+template <class T, int DIR>
+__global__ void __launch_bounds__(kFieldThreads<T>, 1)
+    k_fft_field(cv<T> *a, int n, int logn, const cv<T> *__restrict__ tw)
+{
+    fft_field_body<T, DIR>(a + (size_t)blockIdx.y * n, n, logn, tw);
+}
+
 template <class T>
 __global__ void k_mul_table(cv<T> *a, const cv<T> *__restrict__ tab, int total)
 {
@@ -428,6 +527,19 @@ __global__ void kb_fft_rows(const PlainInst *__restrict__ insts, int mode, int n
                           n, P, Q, logQ, logn, B, (const cv<T> *)I.tw, blockIdx.x);
 }
 
+// grid (1, F, members): whole-field transforms of the buffer of `mode`
+template <class T, int DIR>
+__global__ void __launch_bounds__(kFieldThreads<T>, 1)
+    kb_fft_field(const PlainInst *__restrict__ insts, int mode, int n, int F, int logn)
+{
+    const PlainInst &I = insts[blockIdx.z];
+    int count;
+    cv<T> *a = visit_buffer<T>(I, mode, n, F, &count);
+    if ((int)blockIdx.y >= count)
+        return;
+    fft_field_body<T, DIR>(a + (size_t)blockIdx.y * n, n, logn, (const cv<T> *)I.tw);
+}
+
 // kc >= 0: dispersion factors of crystal kc; kc < 0: the cavity spectral
 // factors (members whose visit transforms every field)
 template <class T>
@@ -525,15 +637,24 @@ int blocks_for(int64_t work)
     return (int)(b < 1 ? 1 : (b > 1184 ? 1184 : b));
 }
 
-// FFT plan of length N = P Q: column/row batch sizes and shared memory.
+// FFT plan of length N: a field of N <= 2^14 (FP32) or 2^13 (FP64) points,
+// and at least 2^8, is transformed whole in one CTA (one kernel, N/16
+// threads, the field in shared memory); larger fields as N = P Q in two
+// kernels (column pass, row pass) with their batch sizes and shared memory.
 struct FFTShape {
     int n, logn, P, Q, logP, logQ, Bc, Br;
     size_t smc, smr;
+    bool whole;       // one kernel per transform
+    size_t smf;       // its shared memory (the padded field)
+    int vpt;          // its values per thread (N/vpt threads)
     template <class T>
     void init(int n_)
     {
         n = n_;
         logn = ilog2((unsigned)n);
+        whole = logn >= 8 && logn <= (sizeof(T) == 8 ? 13 : 14);
+        smf = (size_t)(n + n / 16) * sizeof(cv<T>);
+        vpt = 16;
         logP = logn / 2;
         logQ = logn - logP;
         P = 1 << logP;
@@ -559,6 +680,10 @@ struct PlainFFT {
     template <int DIR>
     void run(cv<T> *a, cv<T> *s, int count, cudaStream_t st) const
     {
+        if (sh.whole) {
+            k_fft_field<T, DIR><<<dim3(1, count), sh.n / sh.vpt, sh.smf, st>>>(a, sh.n, sh.logn, tw);
+            return;
+        }
         dim3 gc(sh.Q / sh.Bc, count), gr(sh.P / sh.Br, count);
         k_fft_cols<T, DIR><<<gc, kThreads, sh.smc, st>>>(a, s, sh.n, sh.P, sh.Q, sh.logP, sh.logn,
                                                           sh.Bc, tw);
@@ -666,6 +791,14 @@ int enqueue_rt_batch(const opo_ctx *c0, const PlainInst *I, int count, cudaStrea
     sh.template init<T>(n);
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
     auto fft = [&](int dir, int mode) {
+        if (sh.whole) {
+            const dim3 gf(1, F, count);
+            if (dir < 0)
+                kb_fft_field<T, -1><<<gf, sh.n / sh.vpt, sh.smf, st>>>(I, mode, n, F, sh.logn);
+            else
+                kb_fft_field<T, 1><<<gf, sh.n / sh.vpt, sh.smf, st>>>(I, mode, n, F, sh.logn);
+            return;
+        }
         dim3 gc(sh.Q / sh.Bc, F, count), gr(sh.P / sh.Br, F, count);
         if (dir < 0) {
             kb_fft_cols<T, -1><<<gc, kThreads, sh.smc, st>>>(I, mode, n, F, sh.P, sh.Q, sh.logP,
@@ -720,6 +853,11 @@ void prepare()
     cudaFuncSetAttribute(kb_fft_cols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(kb_fft_rows<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(kb_fft_rows<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    const int whole = (int)((sizeof(T) == 8 ? 8704 : 17408) * sizeof(cv<T>));
+    cudaFuncSetAttribute(k_fft_field<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, whole);
+    cudaFuncSetAttribute(k_fft_field<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, whole);
+    cudaFuncSetAttribute(kb_fft_field<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, whole);
+    cudaFuncSetAttribute(kb_fft_field<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, whole);
 }
 
 } // namespace

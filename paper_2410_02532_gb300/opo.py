@@ -96,6 +96,7 @@ _SIGS = {
     "opo_batch_create": ([ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
                           ctypes.c_int32], ctypes.c_int),
     "opo_batch_run": ([_P, ctypes.c_int64], ctypes.c_int),
+    "opo_batch_set_one_launch": ([_P, ctypes.c_int32], ctypes.c_int),
     "opo_batch_destroy": ([_P], ctypes.c_int),
     "opo_batch_set_fields": ([_P, _DP, ctypes.c_size_t], ctypes.c_int),
     "opo_batch_get_fields": ([_P, ctypes.c_int32, ctypes.c_int32, _DP, ctypes.c_size_t],
@@ -248,6 +249,10 @@ def opo_batch_create(ctxs, cluster: int = 0, threads: int = 0):
 
 def opo_batch_run(batch, m: int):
     _check(lib().opo_batch_run(batch, int(m)), "opo_batch_run")
+
+
+def opo_batch_set_one_launch(batch, on=True):
+    _check(lib().opo_batch_set_one_launch(batch, 1 if on else 0), "opo_batch_set_one_launch")
 
 
 def opo_batch_destroy(batch):

@@ -20,6 +20,10 @@ It runs ``--rt`` round trips (0 .. rt-1) from the noise start and stores in
                  tolerance scale; floored at half a bin by the test)
   window_drift   relative change of the mean P_s,out between the last two
                  K-round-trip windows (how far from stationary the mean is)
+  centroid_window_drift_hz  change of the mean centroid between those windows
+                 (the signal spectrum keeps walking slowly after the power
+                 has settled, so GPU and oracle are compared after the same
+                 number of round trips)
   p_s_every_10   output signal power at every 10th round trip
 
   python tests/golden/make_steady_state.py [--rt 3000] [--trace FILE.npy]
@@ -89,6 +93,7 @@ def main():
         "centroid_mean_hz": float(full[-K:, 3].mean()),
         "width_hz": width,
         "window_drift": float(abs(last - prev) / last),
+        "centroid_window_drift_hz": float(full[-K:, 3].mean() - full[-2 * K:-K, 3].mean()),
         "p_s_every_10": [float(v) for v in full[9::10, 1]],
         "oracle_seconds": time.time() - t0,
     }

@@ -628,3 +628,40 @@ def test_fused_global_exchange_batch_resume_bitwise(prec):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_one_launch_sweep():
+    """The mixed-size sweep in one persistent launch (generic fused kernel, one
+    cluster size for all): each member within tolerance of the oracle per
+    pass, the same batch run twice gives the same bits, and switching back to
+    one launch per size class gives each member's lone result bit for bit."""
+    cfgs = [cfg_dispersive(n=4096, nz=3), cfg_degenerate(n=8192).replace(nz=3),
+            cfg_dispersive(n=16384, nz=2).replace(delay=5e-15), cfg_dro(n=32768).replace(nz=2)]
+    starts = [strong(c, 2e6, i) for i, c in enumerate(cfgs)]
+
+    def batch_run(one):
+        ctxs = [opo.Context(c, fields=a) for c, a in zip(cfgs, starts)]
+        try:
+            b = opo.opo_batch_create([c.h for c in ctxs], 0, 0)
+            opo.opo_batch_set_one_launch(b, one)
+            opo.opo_batch_run(b, 1)
+            out = [(c.get_fields(), c.get_fields(opo.OPO_OUTPUT), c.trace(1), c.run(0)) for c in ctxs]
+            opo.opo_batch_destroy(b)
+            return out
+        finally:
+            for c in ctxs:
+                c.close()
+
+    one = batch_run(True)
+    for cfg, a, got in zip(cfgs, starts, one):
+        got = (got[0], got[1], got[2], None)
+        compare(cfg, got, oracle_rt(cfg, a), opo.OPO_FP32_PH64, "one_launch n=%d" % cfg.n,
+                test="one_launch")
+    again = batch_run(True)
+    for x, y in zip(one, again):
+        assert np.array_equal(x[0], y[0])
+    per_class = batch_run(False)
+    for cfg, a, got in zip(cfgs, starts, per_class):
+        with opo.Context(cfg, fields=a) as ctx:
+            ctx.run(1)
+            assert np.array_equal(ctx.get_fields(), got[0])
