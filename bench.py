@@ -34,12 +34,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SSFM field-steps/s at N=2^14 (fused, batched round trips)"
 # (instances, cluster, threads requested) -> DRAM bytes per fused launch of the
-# 2^14 workload, from ncu captures of the current kernel: 4-CTA clusters of
-# 512 threads 48.13 MB read + 1.00 MB written (threads 0 = the library's
-# default, 512, for this shape); 8-CTA clusters of 128 threads 48.11 MB read +
-# 0.66 MB written
-PROFILED_SHAPES = {(36, 4, 0): 49.13152e6, (36, 4, 512): 49.13152e6,
-                   (36, 8, 128): 48.769536e6}
+# 2^14 workload (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture of the current kernel in that launch shape): 8-CTA clusters of 128
+# threads, 48.14 MB read + 0.62 MB written
+PROFILED_SHAPES = {(36, 8, 128): 48768000.0}
 UNIT = "field-steps/s"
 PEAK_SM_MHZ = 2070.0          # GB300 maximum SM clock
 SMS = 152
@@ -57,6 +55,13 @@ def parse():
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0: default)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--workload", choices=["cw_sro_16k", "sync_pumped_131072"],
+                    default="cw_sro_16k",
+                    help="the timed batch's workload (default: the 2^14 CW SRO; the other is the "
+                         "2^17-point sync-pumped OPO, for profiling its kernel)")
+    ap.add_argument("--path", choices=["fused", "plain"], default="fused",
+                    help="fused persistent kernel (default) or the batched plain chain, for "
+                         "profiling")
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the headline number (no plain/e2e/cpu legs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -239,13 +244,21 @@ def main():
     stream = torch.cuda.Stream()
     prec = opo.OPO_FP32_PH64 if args.precision == "fp32" else opo.OPO_FP64
     base = W.cw_sro_16k()
+    if args.workload == "sync_pumped_131072":
+        base = W.sync_pumped_64k(delay_fs=5.0).replace(
+            n=1 << 17, name="sync_pumped_n131072_3f_L1mm_nz64_eom")
+    plain = args.path == "plain"
 
     def make(i, s=stream):
         c = base.replace(instance=rank * 100000 + i)
-        return opo.Context(c, precision=prec, device=local, stream=s.cuda_stream if s else None)
+        ctx = opo.Context(c, precision=prec, device=local, stream=s.cuda_stream if s else None)
+        if plain:
+            ctx.set_path(opo.OPO_PATH_PLAIN)
+        return ctx
 
     tuned = None
-    if not args.no_tune and args.cluster == 0 and args.threads == 0:
+    if (not args.no_tune and args.cluster == 0 and args.threads == 0 and not plain
+            and args.workload == "cw_sro_16k"):
         from paper_2410_02532_gb300 import autotune
         tuned = autotune.tune(base.replace(instance=rank * 100000 + 50000), prec, device=local)
     cl_req = tuned["cluster"] if tuned else args.cluster
@@ -290,7 +303,8 @@ def main():
     # dram__bytes_write.sum) from one ncu capture of this workload in this
     # launch shape; reported only when the run uses that shape
     traffic = None
-    if (B, cluster, th_req) in PROFILED_SHAPES and prec == opo.OPO_FP32_PH64:
+    if ((B, cluster, th_req) in PROFILED_SHAPES and prec == opo.OPO_FP32_PH64 and not plain
+            and args.workload == "cw_sro_16k"):
         traffic = PROFILED_SHAPES[(B, cluster, th_req)]
     flops_rt = flops_per_roundtrip(base)
     achieved = flops_rt * B / (statistics.median(step_ms) * 1e-3) / 1e12
@@ -300,6 +314,14 @@ def main():
                 "note": "FP32 vector peak from 152 SMs x 128 lanes x 2 x 2070 MHz; achieved = "
                         "algorithmic FLOPs of the batch round trip / median step time "
                         "(the fused kernel plus one finalize launch)"}
+    if plain:
+        hbm, src = measured_hbm_gbs()
+        gbs = plain_bytes_per_roundtrip(base, 16 if prec == opo.OPO_FP64 else 8) * B / (
+            statistics.median(step_ms) * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": gbs / hbm, "traffic": None,
+                    "note": "batched plain chain; algorithmic bytes / median step time; peak: "
+                            "%s copy bandwidth" % src}
 
     extras = {}
     if not args.skip_extras and rank == 0:
@@ -328,8 +350,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == opo.OPO_FP32_PH64 else "f64",
             "data": "synthetic (seeded noise, random-phase start)",
-            "config": {"workload": "%s x %d instances per GPU (one cluster of %d CTAs each)"
-                                   % (base.name, B, cluster),
+            "config": {"workload": ("%s x %d instances per GPU (one cluster of %d CTAs each)"
+                                    % (base.name, B, cluster)) if not plain else
+                                   ("%s x %d instances per GPU, batched plain chain"
+                                    % (base.name, B)),
                        "n": base.n, "fields": base.nfields, "nz": base.nz,
                        "instances_per_gpu": B, "cluster": cluster,
                        "threads_per_cta": th_req, "autotuned": tuned,

@@ -277,7 +277,8 @@ int check_err(opo_ctx *c)
     if (cudaMemcpy(&err, (char *)c->d_ctl + offsetof(DevCtl, err), sizeof(int),
                    cudaMemcpyDeviceToHost) != cudaSuccess)
         return OPO_E_CUDA;
-    return err ? OPO_E_NONFINITE : OPO_OK;
+    // bit 0: a non-finite field; bit 1: a bounded device wait gave up
+    return err ? ((err & 2) ? OPO_E_TIMEOUT : OPO_E_NONFINITE) : OPO_OK;
 }
 
 int build_graph(opo_ctx *c)
@@ -1180,10 +1181,10 @@ int batch_check_err(opo_batch *b)
         return OPO_E_CUDA;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess)
         return OPO_E_CUDA;
+    int any = 0;
     for (int v : e)
-        if (v)
-            return OPO_E_NONFINITE;
-    return OPO_OK;
+        any |= v;
+    return any ? ((any & 2) ? OPO_E_TIMEOUT : OPO_E_NONFINITE) : OPO_OK;
 }
 
 // A member's state no longer matches the group it was put in (its crystals

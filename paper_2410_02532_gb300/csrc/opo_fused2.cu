@@ -64,7 +64,10 @@ bool ip_config(bool dbl, int nl, int F, int logn, int C, int threads_req, FusedC
     const int A2 = f2::f2_col_a2(LP), A1 = LP - A2;
     const int Qc = (1 << LQ) / C;
     const int nc = (1 << logn) / C;
-    const int maxT = dbl ? 256 : (logn >= 16 ? 384 : f2::F2IpTraits<float>::kMaxThreads);
+    const int maxT = dbl ? 256
+                         : (logn >= 16 ? 384
+                                       : (F == 3 && LP == 7 && nl != kNlKerr ? 256
+                                                                   : f2::F2IpTraits<float>::kMaxThreads));
     (void)A2;
     const size_t csz = dbl ? sizeof(double2) : sizeof(float2);
     const int LS = (logn + 1) / 2;

@@ -22,7 +22,8 @@ struct DevCtl {
     int64_t slot;     // round trip within the current call
     double *obs;      // raw sums [slot][parts][kNslot]
     int32_t parts;    // partial sums per slot (CTAs per instance; 1 on the plain path)
-    int32_t err;      // sticky error word: 1 = non-finite field
+    int32_t err;      // sticky error word: bit 0 a non-finite field, bit 1 a
+                      // bounded device wait that gave up
 };
 
 // Scalars of one instance derived once on the host from crystal and cavity.

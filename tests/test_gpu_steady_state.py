@@ -10,6 +10,7 @@ run.
 import numpy as np
 import pytest
 
+import parity_log
 from oracle import oracle as orc
 from paper_2410_02532_gb300 import opo
 from paper_2410_02532_gb300 import workloads as W
@@ -137,6 +138,14 @@ def test_n16384_from_noise_through_saturation(prec, path):
         tr = ctx.trace(M)
     fp64 = prec == opo.OPO_FP64
     tol = 1e-6 if fp64 else 1e-3
+    parity_log.record("steady_state", "cw_sro_16k_%d_rt" % M, prec, path, n=cfg.n,
+                      fields=cfg.nfields, nz=cfg.nz,
+                      rel_power_signal=abs(tr[-K:, 1].mean() / ref["p_out_mean_W"][1] - 1),
+                      pump_dev_over_input=abs(tr[-K:, 0].mean() - ref["p_out_mean_W"][0])
+                      / cfg.pump_power,
+                      centroid_rel=abs(tr[-K:, 3].mean() / ref["centroid_mean_hz"] - 1),
+                      centroid_over_width=abs(tr[-K:, 3].mean() - ref["centroid_mean_hz"])
+                      / ref["width_hz"])
     ps, ps_ref = tr[-K:, 1].mean(), ref["p_out_mean_W"][1]
     assert abs(ps - ps_ref) <= tol * ps_ref, (ps, ps_ref)
     # the pump's depletion, in units of the input pump power
