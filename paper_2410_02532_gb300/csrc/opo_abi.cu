@@ -277,7 +277,7 @@ int check_err(opo_ctx *c)
     if (cudaMemcpy(&err, (char *)c->d_ctl + offsetof(DevCtl, err), sizeof(int),
                    cudaMemcpyDeviceToHost) != cudaSuccess)
         return OPO_E_CUDA;
-    // bit 0: a non-finite field; bit 1: a bounded device wait gave up
+    // bit 0: a non-finite field; bit 1 (reserved): a bounded device wait gave up
     return err ? ((err & 2) ? OPO_E_TIMEOUT : OPO_E_NONFINITE) : OPO_OK;
 }
 

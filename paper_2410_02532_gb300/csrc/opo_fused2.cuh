@@ -63,76 +63,11 @@ template <> struct F2IpTraits<double> {
     static constexpr int kMaxThreads = 256;
 };
 constexpr int kMaxCl = 16;
-#ifndef OPO_ASYNC_EXCHANGE
-#define OPO_ASYNC_EXCHANGE 0
-#endif
 
 template <int R, int DIR, class V>
 __device__ __forceinline__ void dft_r(V *v)
 {
     dft<R, DIR>(v);
-}
-
-// ---- asynchronous cluster exchange (PTX): a push is an st.async into the
-// owner CTA's shared memory that counts its bytes on the owner's mbarrier;
-// buffer-free signals are remote mbarrier arrivals.  Addresses are 32-bit
-// shared::cluster addresses.
-__device__ __forceinline__ uint32_t as_smem(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint32_t as_mapa(uint32_t a, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void as_store(uint32_t addr, float2 v, uint32_t mbar)
-{
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
-                 ::"r"(addr), "f"(v.x), "f"(v.y), "r"(mbar)
-                 : "memory");
-}
-__device__ __forceinline__ void as_store(uint32_t addr, double2 v, uint32_t mbar)
-{
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
-                 ::"r"(addr), "d"(v.x), "d"(v.y), "r"(mbar)
-                 : "memory");
-}
-__device__ __forceinline__ void as_init(uint32_t a, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void as_expect(uint32_t a, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void as_arrive_remote(uint32_t a)
-{
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ bool as_try(uint32_t a, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n"
-                 " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok)
-                 : "r"(a), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-// Wait for the phase of parity `parity` of the local mbarrier at `a`; gives up
-// after a bounded number of polls (each try_wait suspends for a while) and
-// sets bit 2 of the instance's error word (OPO_E_TIMEOUT), so that a lost
-// signal ends the launch instead of hanging the GPU.
-__device__ __forceinline__ void as_wait(uint32_t a, uint32_t parity, int *err)
-{
-    for (int i = 0; i < (1 << 22); i++)
-        if (as_try(a, parity))
-            return;
-    atomicOr(err, 2);
 }
 
 template <class T, bool IP>
@@ -222,16 +157,6 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
     double *red = reinterpret_cast<double *>(twHi + (N >> LS));
     __shared__ V *rX[kMaxCl];
     __shared__ V *rY[kMaxCl];
-    // asynchronous exchange (in place, DSMEM, four or more CTAs): the owners'
-    // X and Y and mbarriers as shared::cluster addresses, and this CTA's
-    // mbarriers: bytes arriving into Y (mbY) and into X (mbX), and the C
-    // "buffer free" arrivals before pushing into the owners' Y (yfree) and X
-    // (xfree)
-    constexpr bool ASX = IP && !XG && OPO_ASYNC_EXCHANGE;
-    __shared__ uint32_t aX[ASX ? kMaxCl : 1], aY[ASX ? kMaxCl : 1];
-    __shared__ uint32_t aMbX[ASX ? kMaxCl : 1], aMbY[ASX ? kMaxCl : 1];
-    __shared__ uint32_t aXf[ASX ? kMaxCl : 1], aYf[ASX ? kMaxCl : 1];
-    __shared__ __align__(8) unsigned long long mbar[4]; // mbY, mbX, yfree, xfree
 
     // ---- descriptor scalars into registers
     const InstDesc &dg = descs[inst];
@@ -300,31 +225,6 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
     if (threadIdx.x < C) {
         rX[threadIdx.x] = cluster.map_shared_rank(X, (unsigned)threadIdx.x);
         rY[threadIdx.x] = cluster.map_shared_rank(Y, (unsigned)threadIdx.x);
-    }
-    const bool asx = ASX && C >= 4; // cluster-uniform
-    const uint32_t mbY = as_smem(&mbar[0]), mbX = as_smem(&mbar[1]);
-    const uint32_t mbYf = as_smem(&mbar[2]), mbXf = as_smem(&mbar[3]);
-    const uint32_t xbytes = (uint32_t)(F * NC * sizeof(V)); // one exchange into a CTA
-    uint32_t pY = 0, pX = 0, pYf = 0, pXf = 0;              // phase parities
-    if constexpr (ASX) {
-        if (asx) {
-            if ((int)threadIdx.x < C) {
-                const unsigned d = threadIdx.x;
-                aX[d] = as_mapa(as_smem(X), d);
-                aY[d] = as_mapa(as_smem(Y), d);
-                aMbY[d] = as_mapa(mbY, d);
-                aMbX[d] = as_mapa(mbX, d);
-                aYf[d] = as_mapa(mbYf, d);
-                aXf[d] = as_mapa(mbXf, d);
-            }
-            if (threadIdx.x == 0) {
-                as_init(mbY, 1);
-                as_init(mbX, 1);
-                as_init(mbYf, C);
-                as_init(mbXf, C);
-                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            }
-        }
     }
     if (disp_smem) {
         for (int i = threadIdx.x; i < F * NC; i += blockDim.x) {
@@ -722,14 +622,6 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
                     *reinterpret_cast<V *>(t.p + (a0 ^ t.x)) = cmul(v[r], w);
                     w = cmul(w, step);
                 }
-            } else if (ASX && asx) {
-#pragma unroll
-                for (int r = 0; r < Ra2; r++) {
-                    const int k1 = j + r * Ra1, d = k1 >> logPc;
-                    as_store(aY[d] + (uint32_t)(sizeof(V) * RI(f, k1 & (Pc - 1), n2)),
-                             cmul(v[r], w), aMbY[d]);
-                    w = cmul(w, step);
-                }
             } else {
 #pragma unroll
                 for (int r = 0; r < Ra2; r++) {
@@ -973,14 +865,6 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
                     *reinterpret_cast<V *>(t.p + (a0 ^ t.x)) = cmul(v[r], w);
                     w = cmul(w, step);
                 }
-            } else if (ASX && asx) {
-#pragma unroll
-                for (int r = 0; r < Rb1; r++) {
-                    const int n2 = j + r * Rb2, d = n2 >> logQc;
-                    as_store(aX[d] + (uint32_t)(sizeof(V) * CI(f, k1, n2 & (Qc - 1))),
-                             cmul(v[r], w), aMbX[d]);
-                    w = cmul(w, step);
-                }
             } else {
 #pragma unroll
                 for (int r = 0; r < Rb1; r++) {
@@ -1063,52 +947,16 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
             __threadfence();
         cluster.sync();
     };
-    // Asynchronous exchange: before pushing into the owners' Y a CTA waits
-    // until every CTA has read its own Y (yfree, signalled after their
-    // inverse push); after its own push phase it tells every CTA that its X
-    // may be written (xfree), then waits for the bytes of its Y (mbY) and
-    // arms mbY for the next exchange; the inverse half mirrors this.  No CTA
-    // waits at a cluster-wide barrier: the free signals travel half a step
-    // ahead of the pushes that need them.
-    auto signal_all = [&](const uint32_t *a) {
-        if (threadIdx.x == 0)
-            for (int d = 0; d < C; d++)
-                as_arrive_remote(a[d]);
-    };
     auto middle = [&](auto cav_tag, double *acc, int kc) {
         __syncthreads();
-        if (ASX && asx) {
-            as_wait(mbYf, pYf, err);
-            pYf ^= 1;
-            phase2();
-            __syncthreads();
-            signal_all(aXf);
-            as_wait(mbY, pY, err);
-            pY ^= 1;
-            if (threadIdx.x == 0)
-                as_expect(mbY, xbytes);
-        } else {
-            phase2();
-            xsync();
-        }
+        phase2();
+        xsync();
         phase3();
         __syncthreads();
         block_b(cav_tag, acc, kc);
         __syncthreads();
-        if (ASX && asx) {
-            as_wait(mbXf, pXf, err);
-            pXf ^= 1;
-            phase5();
-            __syncthreads();
-            signal_all(aYf);
-            as_wait(mbX, pX, err);
-            pX ^= 1;
-            if (threadIdx.x == 0)
-                as_expect(mbX, xbytes);
-        } else {
-            phase5();
-            xsync();
-        }
+        phase5();
+        xsync();
         phase6();
         __syncthreads();
     };
@@ -1120,14 +968,6 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
     using M5 = std::integral_constant<int, 5>;
     using M6 = std::integral_constant<int, 6>;
     cluster.sync(); // every CTA of the cluster is running; tables loaded
-    if (ASX && asx) {
-        // arm the first exchanges; every CTA's Y is free to begin with
-        if (threadIdx.x == 0) {
-            as_expect(mbY, xbytes);
-            as_expect(mbX, xbytes);
-        }
-        signal_all(aYf);
-    }
     double dummy[kNslot] = {0, 0, 0, 0, 0};
     // mode 0 enters round trip m_start + r_base (its m_cav is the one before)
     set_crystal(0);
@@ -1169,10 +1009,6 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
         set_crystal(0);
         block_a(M3{}, 0, 0, m, r + 1 < M, false, dummy);
     }
-    // asynchronous exchange: the last free signals target other CTAs'
-    // shared memory; no CTA leaves while they may be in flight
-    if (ASX && asx)
-        cluster.sync();
 }
 
 template <class T, int F, int LP, int LQ, bool IP, int NL, bool XG>

@@ -22,8 +22,10 @@ struct DevCtl {
     int64_t slot;     // round trip within the current call
     double *obs;      // raw sums [slot][parts][kNslot]
     int32_t parts;    // partial sums per slot (CTAs per instance; 1 on the plain path)
-    int32_t err;      // sticky error word: bit 0 a non-finite field, bit 1 a
-                      // bounded device wait that gave up
+    int32_t err;      // sticky error word: bit 0 a non-finite field; bit 1 is
+                      // reserved for a bounded device wait that gave up (the
+                      // kernels hold no such wait: clusters meet only at
+                      // hardware cluster barriers)
 };
 
 // Scalars of one instance derived once on the host from crystal and cavity.
