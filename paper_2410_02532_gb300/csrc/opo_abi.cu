@@ -220,6 +220,8 @@ int derive(opo_ctx *c)
         cd.nz = ki.nz;
         cd.use_dk = ki.dk_per_m != 0.0;
         cd.kerr = kerr_coefficients(ki, c->F, cd.kerr_g);
+        for (int x = 0; x < 13; x++)
+            cd.kf[x] = (float)(x < 3 ? cd.kappa[x] : x == 3 ? cd.h : cd.kerr_g[x - 4]);
         c->kerr_any = c->kerr_any || cd.kerr;
         c->dk_any = c->dk_any || cd.use_dk;
     }

@@ -52,6 +52,8 @@ struct CryDesc {
     double kappa[3], h; // 2 pi d_eff / (n lambda); RK4 half step dz/2
     int nz, use_dk, kerr;
     double kerr_g[9];   // Kerr coefficients G_xy, row-major
+    float kf[13];       // kappa[0..2], h, kerr_g[0..8] rounded to float (the
+                        // constants of the FP32 kernels, converted on the host)
 };
 
 // Tables of a crystal after the first (the first one's live in the

@@ -7,9 +7,9 @@
 // and is captured once into a CUDA graph that every round trip replays.
 //
 // An FFT of a field that fits one CTA's shared memory (2^8 <= N <= 2^14 in
-// FP32, 2^13 in FP64; N/16 threads) is one kernel: the field is loaded once, every
-// Stockham stage (radix 2..8) runs in place in shared memory, and it is
-// stored once.  Larger fields (N = P Q) take two kernels (four-step
+// FP32, 2^13 in FP64; N/32 or N/16 threads) is one kernel: the field is
+// loaded once, every Stockham stage (radix 2..8) runs in place in shared
+// memory, and it is stored once.  Larger fields (N = P Q) take two kernels (four-step
 // decomposition, n = Q n1 + n2, k = k1 + P k2): P-point column transforms
 // with the twiddle W_N^{n2 k1} written to scratch, then Q-point row
 // transforms written back in natural order, each kernel transforming a batch
@@ -23,6 +23,7 @@
 // design over many instances at once.  Per element both do the same
 // arithmetic, so a member advances bit for bit as it would alone.
 #include <algorithm>
+#include <type_traits>
 
 #include "opo_common.cuh"
 #include "opo_internal.h"
@@ -55,18 +56,31 @@ __device__ __forceinline__ void entry_body(cv<T> *fields, const cv<T> *pump, int
     }
 }
 
-// One RK4 step of h = dz/2 on every point (the nonlinear half step).
+// One RK4 step of h = dz/2 on every point (the nonlinear half step).  A
+// thread takes two points per iteration (points j and j + stride, their
+// loads issued together), and the grid is sized for a few iterations per
+// thread: the step is short, so a thread's loads must be in flight together.
 template <class T, int F>
 __device__ __forceinline__ void rk4_body(cv<T> *fields, int n, const cv<T> *ekz, int q0, T h,
                                          const T *kap, bool use_e, bool kerr, const T *G)
 {
     using V = cv<T>;
-    V e0 = ekz[q0], e1 = ekz[q0 + 1], e2 = ekz[q0 + 2];
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        V y[F];
+    const V one = cmk<V>((T)1, (T)0);
+    const V e0 = use_e ? ekz[q0] : one, e1 = use_e ? ekz[q0 + 1] : one;
+    const V e2 = use_e ? ekz[q0 + 2] : one;
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += 2 * stride) {
+        const int j2 = j + stride;
+        const bool two = j2 < n;
+        V y[F], z[F];
 #pragma unroll
         for (int x = 0; x < F; x++)
             y[x] = fields[(size_t)x * n + j];
+        if (two) {
+#pragma unroll
+            for (int x = 0; x < F; x++)
+                z[x] = fields[(size_t)x * n + j2];
+        }
         if (kerr)
             rk4_point_kerr<F>(y, e0, e1, e2, kap, h, use_e, G);
         else
@@ -74,6 +88,15 @@ __device__ __forceinline__ void rk4_body(cv<T> *fields, int n, const cv<T> *ekz,
 #pragma unroll
         for (int x = 0; x < F; x++)
             fields[(size_t)x * n + j] = y[x];
+        if (two) {
+            if (kerr)
+                rk4_point_kerr<F>(z, e0, e1, e2, kap, h, use_e, G);
+            else
+                rk4_point<F>(z, e0, e1, e2, kap, h, use_e);
+#pragma unroll
+            for (int x = 0; x < F; x++)
+                fields[(size_t)x * n + j2] = z[x];
+        }
     }
 }
 
@@ -159,95 +182,156 @@ __device__ __forceinline__ void fft_rows_body(const cv<T> *__restrict__ src, cv<
     }
 }
 
-// Whole-field transforms: VPT = 16 values per thread, so N/16 threads; the field sits in shared memory with one pad element after
-// every 16 (index i at i + i/16), which spreads the stride-R stores of the
-// early stages over the banks.
-template <class T> constexpr int kFieldVpt = 16;
-__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+// ---- whole-field transform (2^8 <= N <= 2^14 in FP32, 2^13 in FP64)
+// The field sits in one CTA's shared memory and the transform runs as a few
+// register passes of a Stockham FFT (butterfly j of a radix-R pass with
+// stride Ns reads x[j + r N/R], multiplies by W_{Ns R}^{r k}, k = j mod Ns,
+// takes an R-point DFT and writes output r at (j - k) R + k + r Ns): first
+// one pass of the remaining radix 2^(log2 N mod 4) if there is one (Ns = 1:
+// no twiddles), then radix-16 passes.  The first pass reads the field from
+// global memory straight into registers and the last writes it back from
+// registers, so shared memory holds only the intermediate passes (and the
+// twiddle table).  N is a compile-time constant: every index is then a
+// register plus an immediate.
+// VPT values per thread (N/VPT threads): 32 in FP32 (two radix-16
+// butterflies, up to 128 registers at 512 threads), 16 in FP64.
+template <class T> constexpr int kFieldVpt = sizeof(T) == 8 ? 16 : 32;
+template <class T> constexpr int kFieldThreads = 512;
+template <class T> constexpr int kFieldMaxLog = sizeof(T) == 8 ? 13 : 14;
+constexpr int kFieldMinLog = 8;
 
-// One radix-R Stockham stage over the whole field in place: each thread
-// takes VPT/R butterflies, loads all their inputs into registers, waits at a
-// barrier for every other thread to do the same, then stores its outputs
-// over the same buffer.  Butterfly j reads s[j + r N/R], multiplies by
-// W_{Ns R}^{DIR r k} (k = j mod Ns), takes an R-point DFT and stores output r
-// at (j - k) R + k + r Ns.
-template <int R, int VPT, int DIR, class V>
-__device__ __forceinline__ void field_stage(V *s, int n, int Ns, const V *__restrict__ tw,
-                                            int twshift)
+// shared memory: the field with one pad element after every 16 (index i at
+// i + i/16, which spreads the stride-R stores over the banks)
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+// the half-wave twiddle table W_N^i, i < N/2, XOR-swizzled so that lanes
+// reading W_N^{c k} at consecutive k mostly hit distinct banks
+__device__ __forceinline__ int tsw(int i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15); }
+
+__host__ __device__ constexpr int field_lr(int logn, int p)
 {
+    return (logn % 4 != 0 && p == 0) ? logn % 4 : 4;
+}
+__host__ __device__ constexpr int field_npass(int logn) { return logn / 4 + (logn % 4 ? 1 : 0); }
+__host__ __device__ constexpr int field_lns(int logn, int p)
+{
+    return p == 0 ? 0 : field_lns(logn, p - 1) + field_lr(logn, p - 1);
+}
+__host__ __device__ constexpr int field_smem_elems(int logn)
+{
+    return (1 << logn) + (1 << logn) / 16 + (1 << logn) / 2;
+}
+
+// Twiddles of a radix-16 pass for butterfly k: input r is multiplied by
+// W_{16 Ns}^{r k} = W_N^e, e = r k 2^SH < N, each the table's own entry
+// (W_N^{N/2 + i} = -W_N^i): no twiddle is formed from a product of others,
+// whose rounding, repeated every z-step, shifts the long-run solution.
+template <int LOGN, int SH, int DIR, class V>
+__device__ __forceinline__ void field_twiddle16(V *v, const V *tab, int k)
+{
+    constexpr int HALF = (1 << (LOGN - 1)) - 1;
+#pragma unroll
+    for (int r = 1; r < 16; r++) {
+        const int e = (r * k) << SH;
+        V w = tab[tsw(e & HALF)];
+        if (e >> (LOGN - 1)) {
+            w.x = -w.x;
+            w.y = -w.y;
+        }
+        if (DIR > 0)
+            w.y = -w.y;
+        v[r] = cmul(v[r], w);
+    }
+}
+
+// Pass P of the transform; a is the field in global memory, s the padded
+// shared copy, tab the swizzled quarter-wave table.
+template <int LOGN, int P, int VPT, int DIR, class V>
+__device__ __forceinline__ void field_pass(V *a, V *s, const V *tab)
+{
+    constexpr int N = 1 << LOGN, T = N / VPT;
+    constexpr int LR = field_lr(LOGN, P), R = 1 << LR;
+    constexpr int LNS = field_lns(LOGN, P), NS = 1 << LNS;
     constexpr int B = VPT / R; // butterflies per thread
-    const int Lr = n / R;
+    constexpr int LAST = field_npass(LOGN) - 1;
+    constexpr int SH = LOGN - LNS - LR; // W_{Ns R} = W_N^{2^SH}
+    static_assert(NS == 1 || R == 16, "only the first pass has a radix below 16");
     V v[B][R];
 #pragma unroll
     for (int q = 0; q < B; q++) {
-        const int j = threadIdx.x + q * blockDim.x;
-        const int k = j & (Ns - 1);
+        const int j = (int)threadIdx.x + q * T;
 #pragma unroll
         for (int r = 0; r < R; r++)
-            v[q][r] = s[fpad(j + r * Lr)];
-        if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; r++) {
-                V w = tw[(r * k) << twshift];
-                if (DIR > 0)
-                    w.y = -w.y;
-                v[q][r] = cmul(v[q][r], w);
-            }
-        }
+            v[q][r] = P == 0 ? a[j + r * (N / R)] : s[fpad(j + r * (N / R))];
+        if constexpr (NS > 1)
+            field_twiddle16<LOGN, SH, DIR>(v[q], tab, j & (NS - 1));
         dft<R, DIR>(v[q]);
     }
-    __syncthreads();
+    if constexpr (P > 0 && P < LAST)
+        __syncthreads(); // in place: every read of the pass before any write
 #pragma unroll
     for (int q = 0; q < B; q++) {
-        const int j = threadIdx.x + q * blockDim.x;
-        const int k = j & (Ns - 1);
+        const int j = (int)threadIdx.x + q * T;
+        const int k = j & (NS - 1);
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; r++)
-            s[fpad(base + r * Ns)] = v[q][r];
+        for (int r = 0; r < R; r++) {
+            if constexpr (P == LAST)
+                a[base + r * NS] = v[q][r];
+            else
+                s[fpad(base + r * NS)] = v[q][r];
+        }
     }
-    __syncthreads();
+    if constexpr (P < LAST)
+        __syncthreads();
 }
 
-// Whole-field transform of one field (N <= 2^14 in FP32, 2^13 in FP64: the
-// field fits one CTA's shared memory): one load and one store of the field,
-// every Stockham stage in shared memory in between.  blockDim = N/VPT.
-template <class T, int DIR>
-__device__ __forceinline__ void fft_field_body(cv<T> *a, int n, int logn,
-                                               const cv<T> *__restrict__ tw)
+template <int LOGN, int P, int VPT, int DIR, class V>
+__device__ __forceinline__ void field_passes(V *a, V *s, const V *tab)
+{
+    if constexpr (P < field_npass(LOGN)) {
+        field_pass<LOGN, P, VPT, DIR>(a, s, tab);
+        field_passes<LOGN, P + 1, VPT, DIR>(a, s, tab);
+    }
+}
+
+// In-place transform of one field of 2^LOGN points (blockDim = N / VPT);
+// tw is the global table W_N^i, i < N.
+template <class T, int LOGN, int DIR>
+__device__ __forceinline__ void fft_field_body(cv<T> *a, const cv<T> *__restrict__ tw)
 {
     using V = cv<T>;
-    constexpr int VPT = kFieldVpt<T>;
+    constexpr int N = 1 << LOGN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *s = reinterpret_cast<V *>(smem_raw);
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        s[fpad(i)] = a[i];
-    __syncthreads();
-    // stages of radix at most 8 (a radix-16 DFT and its temporaries do not
-    // fit the 64 registers of 1024 threads), the log2 N bits split as evenly
-    // as possible, largest first
-    const int nst = (logn + 2) / 3;
-    int Ns = 1, lg = 0;
-    for (int st = 0; st < nst; st++) {
-        const int lr = logn / nst + (st < logn % nst ? 1 : 0);
-        const int shift = logn - (lg + lr); // tw holds W_N^i: W_{Ns R} = W_N^{N/(Ns R)}
-        switch (lr) {
-        case 1: field_stage<2, VPT, DIR>(s, n, Ns, tw, shift); break;
-        case 2: field_stage<4, VPT, DIR>(s, n, Ns, tw, shift); break;
-        default: field_stage<8, VPT, DIR>(s, n, Ns, tw, shift); break;
-        }
-        Ns <<= lr;
-        lg += lr;
-    }
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        a[i] = s[fpad(i)];
+    V *tab = s + N + N / 16;
+    for (int i = threadIdx.x; i < N / 2; i += blockDim.x)
+        tab[tsw(i)] = tw[i];
+    // the first pass needs no twiddles and writes s only after reading a;
+    // its closing barrier publishes the table as well
+    field_passes<LOGN, 0, kFieldVpt<T>, DIR>(a, s, tab);
 }
 
+// a[i] *= tab[i]: four elements blockDim apart per thread and iteration, so
+// that each thread has eight loads in flight
 template <class T>
 __device__ __forceinline__ void mul_table_body(cv<T> *a, const cv<T> *__restrict__ tab, int total)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
-        a[i] = cmul(a[i], tab[i]);
+    constexpr int U = 4;
+    const int bd = blockDim.x;
+    for (int i = blockIdx.x * U * bd + threadIdx.x; i < total; i += gridDim.x * U * bd) {
+        cv<T> x[U], t[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+            if (i + q * bd < total) {
+                x[q] = a[i + q * bd];
+                t[q] = tab[i + q * bd];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; q++)
+            if (i + q * bd < total)
+                a[i + q * bd] = cmul(x[q], t[q]);
+    }
 }
 
 __device__ __forceinline__ double block_sum(double v, double *red)
@@ -402,16 +486,12 @@ __global__ void k_fft_rows(const cv<T> *__restrict__ in, cv<T> *__restrict__ out
                           logn, B, tw, blockIdx.x);
 }
 
-// threads of a whole-field transform: N/16, at most 2^14/16 (FP32) and
-// 2^13/16 (FP64)
-template <class T> constexpr int kFieldThreads = sizeof(T) == 8 ? 512 : 1024;
-
 // grid (fields): one whole-field transform per CTA, in place
-template <class T, int DIR>
+template <class T, int LOGN, int DIR>
 __global__ void __launch_bounds__(kFieldThreads<T>, 1)
-    k_fft_field(cv<T> *a, int n, int logn, const cv<T> *__restrict__ tw)
+    k_fft_field(cv<T> *a, const cv<T> *__restrict__ tw)
 {
-    fft_field_body<T, DIR>(a + (size_t)blockIdx.y * n, n, logn, tw);
+    fft_field_body<T, LOGN, DIR>(a + ((size_t)blockIdx.y << LOGN), tw);
 }
 
 template <class T>
@@ -471,12 +551,24 @@ __global__ void kb_rk4(const PlainInst *__restrict__ insts, int n, int kc, int q
 {
     const PlainInst &I = insts[blockIdx.z];
     const CryDesc &cd = I.cry[kc];
-    const T kap[3] = {(T)cd.kappa[0], (T)cd.kappa[1], (T)cd.kappa[2]};
+    // the crystal's constants in the field precision (FP32: the copies the
+    // host rounded; a conversion from double on the device issues on the
+    // FP64 pipe, a small fraction of the FP32 rate, and per thread these
+    // conversions outweighed the step itself)
+    T sc[13];
+#pragma unroll
+    for (int i = 0; i < 13; i++) {
+        if constexpr (sizeof(T) == 4)
+            sc[i] = cd.kf[i];
+        else
+            sc[i] = i < 3 ? cd.kappa[i] : i == 3 ? cd.h : cd.kerr_g[i - 4];
+    }
+    const T kap[3] = {sc[0], sc[1], sc[2]};
     T G[9];
 #pragma unroll
     for (int i = 0; i < 9; i++)
-        G[i] = (T)cd.kerr_g[i];
-    rk4_body<T, F>((cv<T> *)I.fields, n, (const cv<T> *)cd.ekz, q0, (T)cd.h, kap, cd.use_dk != 0,
+        G[i] = sc[4 + i];
+    rk4_body<T, F>((cv<T> *)I.fields, n, (const cv<T> *)cd.ekz, q0, sc[3], kap, cd.use_dk != 0,
                    cd.kerr != 0, G);
 }
 
@@ -528,16 +620,36 @@ __global__ void kb_fft_rows(const PlainInst *__restrict__ insts, int mode, int n
 }
 
 // grid (1, F, members): whole-field transforms of the buffer of `mode`
-template <class T, int DIR>
+template <class T, int LOGN, int DIR>
 __global__ void __launch_bounds__(kFieldThreads<T>, 1)
-    kb_fft_field(const PlainInst *__restrict__ insts, int mode, int n, int F, int logn)
+    kb_fft_field(const PlainInst *__restrict__ insts, int mode, int F)
 {
     const PlainInst &I = insts[blockIdx.z];
     int count;
-    cv<T> *a = visit_buffer<T>(I, mode, n, F, &count);
+    cv<T> *a = visit_buffer<T>(I, mode, 1 << LOGN, F, &count);
     if ((int)blockIdx.y >= count)
         return;
-    fft_field_body<T, DIR>(a + (size_t)blockIdx.y * n, n, logn, (const cv<T> *)I.tw);
+    fft_field_body<T, LOGN, DIR>(a + ((size_t)blockIdx.y << LOGN), (const cv<T> *)I.tw);
+}
+
+// f(std::integral_constant<int, L>{}) for the whole-field size L = log2 N
+template <class T, class Fn>
+void with_field_log(int logn, Fn &&f)
+{
+    using std::integral_constant;
+    switch (logn) {
+    case 8: f(integral_constant<int, 8>{}); break;
+    case 9: f(integral_constant<int, 9>{}); break;
+    case 10: f(integral_constant<int, 10>{}); break;
+    case 11: f(integral_constant<int, 11>{}); break;
+    case 12: f(integral_constant<int, 12>{}); break;
+    case 13: f(integral_constant<int, 13>{}); break;
+    case 14:
+        if constexpr (kFieldMaxLog<T> >= 14)
+            f(integral_constant<int, 14>{});
+        break;
+    default: break;
+    }
 }
 
 // kc >= 0: dispersion factors of crystal kc; kc < 0: the cavity spectral
@@ -638,23 +750,23 @@ int blocks_for(int64_t work)
 }
 
 // FFT plan of length N: a field of N <= 2^14 (FP32) or 2^13 (FP64) points,
-// and at least 2^8, is transformed whole in one CTA (one kernel, N/16
+// and at least 2^8, is transformed whole in one CTA (one kernel, N/VPT
 // threads, the field in shared memory); larger fields as N = P Q in two
 // kernels (column pass, row pass) with their batch sizes and shared memory.
 struct FFTShape {
     int n, logn, P, Q, logP, logQ, Bc, Br;
     size_t smc, smr;
     bool whole;       // one kernel per transform
-    size_t smf;       // its shared memory (the padded field)
+    size_t smf;       // its shared memory (the padded field, twiddle tables)
     int vpt;          // its values per thread (N/vpt threads)
     template <class T>
     void init(int n_)
     {
         n = n_;
         logn = ilog2((unsigned)n);
-        whole = logn >= 8 && logn <= (sizeof(T) == 8 ? 13 : 14);
-        smf = (size_t)(n + n / 16) * sizeof(cv<T>);
-        vpt = 16;
+        whole = logn >= kFieldMinLog && logn <= kFieldMaxLog<T>;
+        smf = whole ? (size_t)field_smem_elems(logn) * sizeof(cv<T>) : 0;
+        vpt = kFieldVpt<T>;
         logP = logn / 2;
         logQ = logn - logP;
         P = 1 << logP;
@@ -681,7 +793,12 @@ struct PlainFFT {
     void run(cv<T> *a, cv<T> *s, int count, cudaStream_t st) const
     {
         if (sh.whole) {
-            k_fft_field<T, DIR><<<dim3(1, count), sh.n / sh.vpt, sh.smf, st>>>(a, sh.n, sh.logn, tw);
+            const cv<T> *t = tw;
+            const int threads = sh.n / sh.vpt;
+            const size_t sm = sh.smf;
+            with_field_log<T>(sh.logn, [&](auto L) {
+                k_fft_field<T, decltype(L)::value, DIR><<<dim3(1, count), threads, sm, st>>>(a, t);
+            });
             return;
         }
         dim3 gc(sh.Q / sh.Bc, count), gr(sh.P / sh.Br, count);
@@ -731,6 +848,8 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
     fft.init_raw(n, (const V *)c->d_tw);
     const Derived &d = c->dv;
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
+    const int gM = blocks_for(((int64_t)F * n + 7) / 8); // mul_table: 8 elements a thread
+    const int gR = blocks_for(((int64_t)n + 3) / 4);     // rk4: 4 points a thread
     k_entry<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_pump, n, F, c->cavity.resonant_mask,
                                           c->dv.ns, c->d_ctl);
     // every crystal in order; z of the e^{i dk z} factor restarts in each
@@ -743,16 +862,16 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
             for (int half = 0; half < 2; half++) {
                 int q0 = 4 * j + 2 * half;
                 if (F == 3)
-                    k_rk4<T, 3><<<gN, kThreads, 0, st>>>(fld, n, ekz, q0, hc, (T)cd.kappa[0],
+                    k_rk4<T, 3><<<gR, kThreads, 0, st>>>(fld, n, ekz, q0, hc, (T)cd.kappa[0],
                                                          (T)cd.kappa[1], (T)cd.kappa[2],
                                                          cd.use_dk != 0, cd.kerr != 0, G);
                 else
-                    k_rk4<T, 2><<<gN, kThreads, 0, st>>>(fld, n, ekz, q0, hc, (T)cd.kappa[0],
+                    k_rk4<T, 2><<<gR, kThreads, 0, st>>>(fld, n, ekz, q0, hc, (T)cd.kappa[0],
                                                          (T)cd.kappa[1], (T)cd.kappa[2],
                                                          cd.use_dk != 0, cd.kerr != 0, G);
                 if (half == 0) {
                     fft.template run<-1>(fld, scr, F, st);
-                    k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)cd.disp, F * n);
+                    k_mul_table<T><<<gM, kThreads, 0, st>>>(fld, (const V *)cd.disp, F * n);
                     fft.template run<1>(fld, scr, F, st);
                 }
             }
@@ -768,7 +887,7 @@ int enqueue_rt(opo_ctx *c, cudaStream_t st)
     if (spec_all_fields(c)) {
         fft.template run<-1>(fld, scr, F, st);
         k_spec_sums<T><<<1, 1024, 0, st>>>(sig, n, c->d_ctl);
-        k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)c->d_gdd, F * n);
+        k_mul_table<T><<<gM, kThreads, 0, st>>>(fld, (const V *)c->d_gdd, F * n);
         fft.template run<1>(fld, scr, F, st);
     } else {
         // centroid only: transform a copy of the signal
@@ -790,13 +909,18 @@ int enqueue_rt_batch(const opo_ctx *c0, const PlainInst *I, int count, cudaStrea
     FFTShape sh;
     sh.template init<T>(n);
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
+    const int gM = blocks_for(((int64_t)F * n + 7) / 8); // mul_table: 8 elements a thread
+    const int gR = blocks_for(((int64_t)n + 3) / 4);     // rk4: 4 points a thread
     auto fft = [&](int dir, int mode) {
         if (sh.whole) {
             const dim3 gf(1, F, count);
-            if (dir < 0)
-                kb_fft_field<T, -1><<<gf, sh.n / sh.vpt, sh.smf, st>>>(I, mode, n, F, sh.logn);
-            else
-                kb_fft_field<T, 1><<<gf, sh.n / sh.vpt, sh.smf, st>>>(I, mode, n, F, sh.logn);
+            with_field_log<T>(sh.logn, [&](auto L) {
+                constexpr int LG = decltype(L)::value;
+                if (dir < 0)
+                    kb_fft_field<T, LG, -1><<<gf, sh.n / sh.vpt, sh.smf, st>>>(I, mode, F);
+                else
+                    kb_fft_field<T, LG, 1><<<gf, sh.n / sh.vpt, sh.smf, st>>>(I, mode, F);
+            });
             return;
         }
         dim3 gc(sh.Q / sh.Bc, F, count), gr(sh.P / sh.Br, F, count);
@@ -818,12 +942,12 @@ int enqueue_rt_batch(const opo_ctx *c0, const PlainInst *I, int count, cudaStrea
             for (int half = 0; half < 2; half++) {
                 const int q0 = 4 * j + 2 * half;
                 if (F == 3)
-                    kb_rk4<T, 3><<<dim3(gN, 1, count), kThreads, 0, st>>>(I, n, i, q0);
+                    kb_rk4<T, 3><<<dim3(gR, 1, count), kThreads, 0, st>>>(I, n, i, q0);
                 else
-                    kb_rk4<T, 2><<<dim3(gN, 1, count), kThreads, 0, st>>>(I, n, i, q0);
+                    kb_rk4<T, 2><<<dim3(gR, 1, count), kThreads, 0, st>>>(I, n, i, q0);
                 if (half == 0) {
                     fft(-1, 0);
-                    kb_mul_table<T><<<dim3(gFN, 1, count), kThreads, 0, st>>>(I, n, F, i);
+                    kb_mul_table<T><<<dim3(gM, 1, count), kThreads, 0, st>>>(I, n, F, i);
                     fft(1, 0);
                 }
             }
@@ -834,7 +958,7 @@ int enqueue_rt_batch(const opo_ctx *c0, const PlainInst *I, int count, cudaStrea
     kb_copy_signal<T><<<dim3(gN, 1, count), kThreads, 0, st>>>(I, n);
     fft(-1, 1);
     kb_spec_sums<T><<<dim3(1, 1, count), 1024, 0, st>>>(I, n);
-    kb_mul_table<T><<<dim3(gFN, 1, count), kThreads, 0, st>>>(I, n, F, -1);
+    kb_mul_table<T><<<dim3(gM, 1, count), kThreads, 0, st>>>(I, n, F, -1);
     fft(1, 2);
     kb_cavity_time<T><<<dim3(gN, 1, count), kThreads, 0, st>>>(I, n, F);
     kb_end_rt<<<(count + 255) / 256, 256, 0, st>>>(I, count);
@@ -853,11 +977,16 @@ void prepare()
     cudaFuncSetAttribute(kb_fft_cols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(kb_fft_rows<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(kb_fft_rows<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    const int whole = (int)((sizeof(T) == 8 ? 8704 : 17408) * sizeof(cv<T>));
-    cudaFuncSetAttribute(k_fft_field<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, whole);
-    cudaFuncSetAttribute(k_fft_field<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, whole);
-    cudaFuncSetAttribute(kb_fft_field<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, whole);
-    cudaFuncSetAttribute(kb_fft_field<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, whole);
+    for (int lg = kFieldMinLog; lg <= kFieldMaxLog<T>; lg++) {
+        with_field_log<T>(lg, [&](auto L) {
+            constexpr int LG = decltype(L)::value;
+            const int sm = (int)(field_smem_elems(LG) * sizeof(cv<T>));
+            cudaFuncSetAttribute(k_fft_field<T, LG, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(k_fft_field<T, LG, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(kb_fft_field<T, LG, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaFuncSetAttribute(kb_fft_field<T, LG, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        });
+    }
 }
 
 } // namespace
@@ -955,18 +1084,20 @@ int pass_raw(void *fields, void *scratch, const void *tw, const void *disp, cons
     PlainFFT<T> fft;
     fft.init_raw(n, (const V *)tw);
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
+    const int gM = blocks_for(((int64_t)F * n + 7) / 8); // mul_table: 8 elements a thread
+    const int gR = blocks_for(((int64_t)n + 3) / 4);     // rk4: 4 points a thread
     for (int j = 0; j < nz; j++) {
         for (int half = 0; half < 2; half++) {
             int q0 = 4 * j + 2 * half;
             if (F == 3)
-                k_rk4<T, 3><<<gN, kThreads, 0, st>>>(fld, n, (const V *)ekz, q0, (T)h, (T)kappa[0],
+                k_rk4<T, 3><<<gR, kThreads, 0, st>>>(fld, n, (const V *)ekz, q0, (T)h, (T)kappa[0],
                                                      (T)kappa[1], (T)kappa[2], use_dk, kerr, G);
             else
-                k_rk4<T, 2><<<gN, kThreads, 0, st>>>(fld, n, (const V *)ekz, q0, (T)h, (T)kappa[0],
+                k_rk4<T, 2><<<gR, kThreads, 0, st>>>(fld, n, (const V *)ekz, q0, (T)h, (T)kappa[0],
                                                      (T)kappa[1], (T)kappa[2], use_dk, kerr, G);
             if (half == 0) {
                 fft.template run<-1>(fld, scr, F, st);
-                k_mul_table<T><<<gFN, kThreads, 0, st>>>(fld, (const V *)disp, F * n);
+                k_mul_table<T><<<gM, kThreads, 0, st>>>(fld, (const V *)disp, F * n);
                 fft.template run<1>(fld, scr, F, st);
             }
         }
