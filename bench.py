@@ -264,7 +264,11 @@ def main():
     cl_req = tuned["cluster"] if tuned else args.cluster
     th_req = tuned["threads"] if tuned else args.threads
     probe = make(0)
-    active, cluster = opo.opo_fused_capacity(probe.h, cl_req, th_req)
+    if plain and args.batch > 0:
+        # sizes without a fused form (FP64 at 2^17) have no fused capacity
+        active, cluster = args.batch, args.cluster
+    else:
+        active, cluster = opo.opo_fused_capacity(probe.h, cl_req, th_req)
     B = args.batch if args.batch > 0 else max(1, active)
     # weak scaling: every rank owns its own block of B instances (seeds differ)
     ctxs = [probe] + [make(i) for i in range(1, B)]
