@@ -36,8 +36,8 @@ METRIC = "SSFM field-steps/s at N=2^14 (fused, batched round trips)"
 # (instances, cluster, threads requested) -> DRAM bytes per fused launch of the
 # 2^14 workload (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture of the current kernel in that launch shape): 8-CTA clusters of 128
-# threads, 48.14 MB read + 0.62 MB written
-PROFILED_SHAPES = {(36, 8, 128): 48768000.0}
+# threads (cluster size compiled in), 48.08 MB read + 0.67 MB written
+PROFILED_SHAPES = {(36, 8, 128): 48748288.0}
 UNIT = "field-steps/s"
 PEAK_SM_MHZ = 2070.0          # GB300 maximum SM clock
 SMS = 152
@@ -48,7 +48,7 @@ FP64_NOMINAL_TFLOPS = 1.25    # GB300 FP64 (non-tensor), nominal
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=0, help="instances per GPU (0: fill the GPU)")
@@ -118,10 +118,20 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the timed region starts once the sampler is writing samples
+        t0 = time.time()
+        while time.time() - t0 < 3.0:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
