@@ -549,6 +549,20 @@ LARGE_CASES = [
      opo.OPO_FP64, opo.OPO_PATH_PLAIN),
     ("plain_n65536_dro_loss_dk", lambda: cfg_dro(n=1 << 16).replace(nz=3), opo.OPO_FP32_PH64,
      opo.OPO_PATH_PLAIN),
+    # every whole-field transform size of the plain chain (one kernel
+    # compiled per size: 2^12 = 16^3, 2^13 = 2 x 16^3) and the FP32 two-pass
+    # form at 2^15
+    ("plain_n4096_gdd", lambda: cfg_dispersive(n=1 << 12, nz=4), opo.OPO_FP32_PH64,
+     opo.OPO_PATH_PLAIN),
+    ("plain_n4096_gdd", lambda: cfg_dispersive(n=1 << 12, nz=4), opo.OPO_FP64, opo.OPO_PATH_PLAIN),
+    ("plain_n8192_sync_eom", lambda: cfg_sync(n=8192).replace(nz=4), opo.OPO_FP32_PH64,
+     opo.OPO_PATH_PLAIN),
+    ("plain_n8192_sync_eom", lambda: cfg_sync(n=8192).replace(nz=4), opo.OPO_FP64,
+     opo.OPO_PATH_PLAIN),
+    ("plain_n8192_degenerate_dk", lambda: cfg_degenerate(n=8192).replace(nz=4), opo.OPO_FP32_PH64,
+     opo.OPO_PATH_PLAIN),
+    ("plain_n32768_gdd", lambda: cfg_dispersive(n=1 << 15, nz=3), opo.OPO_FP32_PH64,
+     opo.OPO_PATH_PLAIN),
 ]
 
 
