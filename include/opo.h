@@ -359,11 +359,10 @@ OPO_API int opo_batch_get_trace(opo_batch *batch, double *host, int64_t rows);
  *         of the scratch it reads (nothing must start at zero).  Calls whose
  *         work overlaps on the GPU (other streams, other threads) race on the
  *         shared scratch: serialize them.
- * Set-up: the first call on a device looks up the array's device address with
- *         that device current (no allocation) and keeps it for later calls;
- *         make that first call before any stream capture.  A device reset
- *         (cudaDeviceReset) in the process invalidates the kept address: do
- *         not call this entry point on that device after one. */
+ * Set-up: every call looks up the array's device address with that device
+ *         current (a lookup, no allocation; the first one on a device may
+ *         load the library's device code, so make it before any stream
+ *         capture). */
 OPO_API int opo_crystal_pass_noalloc(const opo_grid *grid, const opo_crystal *crystal,
                                      void *fields, void *stream);
 

@@ -5,7 +5,6 @@
 // intermediate, twiddles, dispersion factors, e^{i dk z} factors) lives in
 // one file-scope device array, so the call itself allocates nothing.
 #include <cmath>
-#include <mutex>
 
 #include "opo_common.cuh"
 #include "opo_internal.h"
@@ -19,23 +18,17 @@ constexpr int kMaxDevices = 64;
 // until the process exits.
 static __device__ __align__(256) unsigned char opo_noalloc_scratch[kScratchBytes];
 
-// Device address of the array, found once per device with that device
-// current (the host-side name of a __device__ array is only a stand-in).
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
-int scratch_for(int dev, void **out)
+// Device address of the array on the current device, looked up on every
+// call (a lookup allocates nothing; a cached address would go stale when
+// the module is loaded again after a device reset).
+int scratch_for(void **out)
 {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, opo_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return OPO_E_CUDA;
-        }
-        g_scratch_ptr[dev] = p;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, opo_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return OPO_E_CUDA;
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return OPO_OK;
 }
 
@@ -75,7 +68,7 @@ extern "C" OPO_API int opo_crystal_pass_noalloc(const opo_grid *grid, const opo_
     if (cudaSetDevice(grid->device) != cudaSuccess)
         return OPO_E_CUDA;
     void *base = nullptr;
-    int rc = scratch_for(grid->device, &base);
+    int rc = scratch_for(&base);
     if (rc == OPO_OK) {
         cudaStream_t s = (cudaStream_t)stream;
         char *b = (char *)base;
