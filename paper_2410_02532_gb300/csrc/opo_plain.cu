@@ -781,7 +781,7 @@ struct FFTShape {
 
 template <class T>
 struct PlainFFT {
-    FFTShape sh;
+    FFTShape sh{};
     const cv<T> *tw;
     void init_raw(int n_, const cv<T> *tw_)
     {
@@ -906,7 +906,7 @@ template <class T>
 int enqueue_rt_batch(const opo_ctx *c0, const PlainInst *I, int count, cudaStream_t st)
 {
     const int n = c0->n, F = c0->F;
-    FFTShape sh;
+    FFTShape sh{};
     sh.template init<T>(n);
     const int gN = blocks_for(n), gFN = blocks_for((int64_t)F * n);
     const int gM = blocks_for(((int64_t)F * n + 7) / 8); // mul_table: 8 elements a thread
