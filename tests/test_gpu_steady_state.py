@@ -154,3 +154,41 @@ def test_n16384_from_noise_through_saturation(prec, path):
     nu, nu_ref = tr[-K:, 3].mean(), ref["centroid_mean_hz"]
     bound = tol * max(ref["width_hz"], 0.5 / cfg.t_window) if fp64 else 0.05 * abs(nu_ref)
     assert abs(nu - nu_ref) <= bound, (nu, nu_ref, bound)
+
+
+# The same workload after 20000 round trips, where the oracle run has
+# settled: tests/golden/steady_state_cw_sro_16k_long.json, written by
+#   python tests/golden/make_steady_state.py --rt 20000 \
+#       --out tests/golden/steady_state_cw_sro_16k_long.json
+# (oracle/ only; about four hours of one core).  Means over the last 2000
+# round trips; FP32 fields with FP64 phases on both paths (the FP64 path
+# tracks the oracle within 1e-6 through the transient above; 20000 of its
+# round trips would take ten minutes here).
+GOLDEN_16K_LONG = os.path.join(os.path.dirname(__file__), "golden",
+                               "steady_state_cw_sro_16k_long.json")
+
+
+@pytest.mark.parametrize("path", [opo.OPO_PATH_FUSED, opo.OPO_PATH_PLAIN], ids=["fused", "plain"])
+def test_n16384_settled_after_20000_round_trips(path):
+    ref = json.load(open(GOLDEN_16K_LONG))
+    cfg = W.cw_sro_16k()
+    assert ref["workload"] == cfg.name
+    M, K = ref["rt"], ref["last"]
+    # the oracle run has settled: the mean output signal power of its last
+    # two K-round-trip windows agree well inside the bar
+    assert ref["window_drift"] < 2e-4, ref["window_drift"]
+    with opo.Context(cfg, precision=opo.OPO_FP32_PH64) as ctx:
+        ctx.set_path(path)
+        ctx.run(M)
+        tr = ctx.trace(M)
+    ps, ps_ref = tr[-K:, 1].mean(), ref["p_out_mean_W"][1]
+    pp, pp_ref = tr[-K:, 0].mean(), ref["p_out_mean_W"][0]
+    nu, nu_ref = tr[-K:, 3].mean(), ref["centroid_mean_hz"]
+    parity_log.record("steady_state", "cw_sro_16k_%d_rt" % M, opo.OPO_FP32_PH64, path, n=cfg.n,
+                      fields=cfg.nfields, nz=cfg.nz, rel_power_signal=abs(ps / ps_ref - 1),
+                      pump_dev_over_input=abs(pp - pp_ref) / cfg.pump_power,
+                      centroid_rel=abs(nu / nu_ref - 1),
+                      centroid_over_width=abs(nu - nu_ref) / ref["width_hz"])
+    assert abs(ps - ps_ref) <= 1e-3 * ps_ref, (ps, ps_ref)
+    assert abs(pp - pp_ref) <= 1e-3 * cfg.pump_power, (pp, pp_ref)
+    assert abs(nu - nu_ref) <= 1e-3 * abs(nu_ref), (nu, nu_ref)
