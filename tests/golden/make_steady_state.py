@@ -27,6 +27,11 @@ It runs ``--rt`` round trips (0 .. rt-1) from the noise start and stores in
   p_s_every_10   output signal power at every 10th round trip
 
   python tests/golden/make_steady_state.py [--rt 3000] [--trace FILE.npy]
+
+The settled state after 20000 round trips (about four hours of one core):
+
+  python tests/golden/make_steady_state.py --rt 20000 \
+      --out tests/golden/steady_state_cw_sro_16k_long.json
 """
 import argparse
 import json

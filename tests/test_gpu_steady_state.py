@@ -156,14 +156,19 @@ def test_n16384_from_noise_through_saturation(prec, path):
     assert abs(nu - nu_ref) <= bound, (nu, nu_ref, bound)
 
 
-# The same workload after 20000 round trips, where the oracle run has
-# settled: tests/golden/steady_state_cw_sro_16k_long.json, written by
+# The same workload after 20000 round trips: tests/golden/
+# steady_state_cw_sro_16k_long.json, written by
 #   python tests/golden/make_steady_state.py --rt 20000 \
 #       --out tests/golden/steady_state_cw_sro_16k_long.json
-# (oracle/ only; about four hours of one core).  Means over the last 2000
-# round trips; FP32 fields with FP64 phases on both paths (the FP64 path
-# tracks the oracle within 1e-6 through the transient above; 20000 of its
-# round trips would take ten minutes here).
+# (oracle/ only; about four hours of one core).  By then the output powers
+# have settled (the mean P_s,out of the last two 2000-round-trip windows
+# differs by 2.5e-7), so the FP32 fields with FP64 phases (both paths) are
+# held to the 1e-3 bar on both powers with the transient gone.  The signal
+# centroid is on a slow excursion (up to 11.2 THz at ~11000 round trips,
+# back to 9.7 THz at 20000, moving ~4% per 2000 round trips) whose rate FP32
+# rounding changes by a few per cent, so it is held to 5% as in the 3000
+# round-trip test.  The FP64 path tracks the oracle within 1e-6 through the
+# transient above; 20000 of its round trips would take ten minutes here.
 GOLDEN_16K_LONG = os.path.join(os.path.dirname(__file__), "golden",
                                "steady_state_cw_sro_16k_long.json")
 
@@ -176,7 +181,7 @@ def test_n16384_settled_after_20000_round_trips(path):
     M, K = ref["rt"], ref["last"]
     # the oracle run has settled: the mean output signal power of its last
     # two K-round-trip windows agree well inside the bar
-    assert ref["window_drift"] < 2e-4, ref["window_drift"]
+    assert ref["window_drift"] < 1e-4, ref["window_drift"]
     with opo.Context(cfg, precision=opo.OPO_FP32_PH64) as ctx:
         ctx.set_path(path)
         ctx.run(M)
@@ -191,4 +196,4 @@ def test_n16384_settled_after_20000_round_trips(path):
                       centroid_over_width=abs(nu - nu_ref) / ref["width_hz"])
     assert abs(ps - ps_ref) <= 1e-3 * ps_ref, (ps, ps_ref)
     assert abs(pp - pp_ref) <= 1e-3 * cfg.pump_power, (pp, pp_ref)
-    assert abs(nu - nu_ref) <= 1e-3 * abs(nu_ref), (nu, nu_ref)
+    assert abs(nu - nu_ref) <= 0.05 * abs(nu_ref), (nu, nu_ref)
