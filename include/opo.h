@@ -338,6 +338,32 @@ OPO_API int opo_batch_get_fields(opo_batch *batch, int32_t field, int32_t which,
                                  size_t count);
 OPO_API int opo_batch_get_trace(opo_batch *batch, double *host, int64_t rows);
 
+/* One step of a batch with its host transfers in flight beside the other
+ * steps' round trips: the main loop of Sec. 4.1 (fields in, round trips,
+ * output fields and observables out) for a stream of batch steps.  The call
+ * only enqueues work and returns:
+ *   1. host_in (if not NULL: every member's F x N start state, layout and
+ *      count as opo_batch_set_fields; page-locked host memory) is copied to a
+ *      device staging slot on a copy stream of the batch, so that the copy
+ *      overlaps the previous step's round trips, then written into the
+ *      members' fields in stream order;
+ *   2. m round trips of every member (as opo_batch_run);
+ *   3. if host_out is not NULL: field `field` of every member's output
+ *      (OPO_OUTPUT, layout as opo_batch_get_fields, sum of N complex) and
+ *      then the last trace row of every member (4 doubles each, members in
+ *      order) are gathered into a device slot and copied to host_out on a
+ *      second copy stream, so that the copy overlaps the next step.
+ * Two staging slots alternate between consecutive calls.  host_in must not
+ * change, and host_out must not be read, until opo_batch_io_wait returns;
+ * consecutive calls may reuse the same host buffers.  opo_batch_io_wait
+ * waits for every enqueued step and copy of the batch and returns
+ * OPO_E_NONFINITE if any member holds a non-finite field.  Errors of the
+ * arguments return before anything is enqueued (OPO_E_INVALID; m >= 1;
+ * 0 <= field < the members' least field count). */
+OPO_API int opo_batch_step_io(opo_batch *batch, const double *host_in, double *host_out,
+                              int32_t field, int64_t m);
+OPO_API int opo_batch_io_wait(opo_batch *batch);
+
 /* One crystal pass without any device allocation, for callers that cannot
  * call cudaMalloc (code that runs inside another framework's memory pool or
  * under an allocator that is locked down or already exhausted).  The paper

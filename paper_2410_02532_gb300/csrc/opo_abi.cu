@@ -128,6 +128,13 @@ __global__ void k_batch_trace(const XMember *m, int count, int rows, double *dst
         dst[e] = m[e / per].trace[e % per];
 }
 
+// Row rows - 1 of every member's trace, members in order (4 doubles each).
+__global__ void k_batch_last_row(const XMember *m, int count, int rows, double *dst)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 4 * count; e += gridDim.x * blockDim.x)
+        dst[e] = m[e / 4].trace[4LL * (rows - 1) + e % 4];
+}
+
 __global__ void k_gather_err(int *const *src, int count, int *dst)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
@@ -934,15 +941,33 @@ struct opo_batch {
     size_t xfer_cap = 0;         // doubles
     XMember *d_mem = nullptr;    // member table of the transfer kernels
     std::vector<XMember> h_mem;
+    std::vector<XMember> h_mem_dev; // what d_mem holds
     int **d_err = nullptr;       // members' sticky error words
     int *d_errs = nullptr;       // their copies, one per member
+    // overlapped host transfers (opo_batch_step_io): two slots each way
+    cudaStream_t io_in = nullptr, io_out = nullptr;
+    double *d_in[2] = {nullptr, nullptr}, *d_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_h2d[2] = {nullptr, nullptr};  // staged input copied in
+    cudaEvent_t ev_used[2] = {nullptr, nullptr}; // staged input consumed
+    cudaEvent_t ev_gath[2] = {nullptr, nullptr}; // output gathered
+    cudaEvent_t ev_d2h[2] = {nullptr, nullptr};  // output copied out
+    int io_slot = 0;
 };
 
 static void batch_free(opo_batch *b)
 {
-    for (void *p : {(void *)b->d_xfer, (void *)b->d_err, (void *)b->d_errs, (void *)b->d_mem})
+    for (void *p : {(void *)b->d_xfer, (void *)b->d_err, (void *)b->d_errs, (void *)b->d_mem,
+                    (void *)b->d_in[0], (void *)b->d_in[1], (void *)b->d_out[0],
+                    (void *)b->d_out[1]})
         if (p)
             cudaFree(p);
+    for (int k = 0; k < 2; k++)
+        for (cudaEvent_t e : {b->ev_h2d[k], b->ev_used[k], b->ev_gath[k], b->ev_d2h[k]})
+            if (e)
+                cudaEventDestroy(e);
+    for (cudaStream_t st : {b->io_in, b->io_out})
+        if (st)
+            cudaStreamDestroy(st);
     for (BatchGroup &g : b->groups) {
         if (g.stream)
             cudaStreamDestroy(g.stream);
@@ -1145,11 +1170,17 @@ int batch_members(opo_batch *b, cudaStream_t s)
         oa += (long long)c->F * c->n;
         on += c->n;
     }
+    // unchanged since the last upload (the usual case between steps of the
+    // same length): nothing to copy
+    if (b->h_mem_dev.size() == b->h_mem.size() &&
+        std::memcmp(b->h_mem_dev.data(), b->h_mem.data(), sizeof(XMember) * count) == 0)
+        return OPO_OK;
     // the pageable source is staged before cudaMemcpyAsync returns
-    return cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(XMember) * count,
-                           cudaMemcpyHostToDevice, s) == cudaSuccess
-               ? OPO_OK
-               : OPO_E_CUDA;
+    if (cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(XMember) * count,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return OPO_E_CUDA;
+    b->h_mem_dev = b->h_mem;
+    return OPO_OK;
 }
 
 int xblocks(long long work)
@@ -1425,6 +1456,105 @@ int opo_batch_run(opo_batch *b, int64_t m)
         }
     }
     return rc;
+}
+
+int opo_batch_step_io(opo_batch *b, const double *host_in, double *host_out, int32_t field,
+                      int64_t m)
+{
+    if (!b || m < 1 || field < 0)
+        return OPO_E_INVALID;
+    size_t n_in = 0, n_out = 0;
+    for (const opo_ctx *c : b->ctxs) {
+        if (field >= c->F || (c->d_hist && m > c->hist_cap))
+            return OPO_E_INVALID;
+        n_in += (size_t)c->F * c->n;
+        n_out += (size_t)c->n;
+    }
+    const int count = (int)b->ctxs.size();
+    const size_t in_doubles = 2 * n_in, out_doubles = 2 * n_out + 4 * (size_t)count;
+    DeviceGuard g(b->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    // first use: the copy streams, events and staging slots
+    if (!b->io_in) {
+        bool ok = cudaStreamCreateWithFlags(&b->io_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&b->io_out, cudaStreamNonBlocking) == cudaSuccess;
+        for (int k = 0; ok && k < 2; k++)
+            ok = cudaEventCreateWithFlags(&b->ev_h2d[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->ev_used[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->ev_gath[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->ev_d2h[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaMalloc((void **)&b->d_in[k], sizeof(double) * in_doubles) == cudaSuccess &&
+                 cudaMalloc((void **)&b->d_out[k], sizeof(double) * out_doubles) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return OPO_E_NOMEM;
+        }
+        for (int k = 0; k < 2; k++) { // nothing pending on either slot yet
+            cudaEventRecord(b->ev_used[k], b->io_in);
+            cudaEventRecord(b->ev_d2h[k], b->io_out);
+        }
+    }
+    const int slot = b->io_slot;
+    cudaStream_t s = b->stream;
+    batch_fence(b, s, true);
+    int rc = batch_members(b, s);
+    if (rc != OPO_OK)
+        return rc;
+    if (host_in) {
+        // the slot's previous input has been consumed two steps ago
+        cudaStreamWaitEvent(b->io_in, b->ev_used[slot], 0);
+        if (cudaMemcpyAsync(b->d_in[slot], host_in, sizeof(double) * in_doubles,
+                            cudaMemcpyHostToDevice, b->io_in) != cudaSuccess)
+            return OPO_E_CUDA;
+        cudaEventRecord(b->ev_h2d[slot], b->io_in);
+        cudaStreamWaitEvent(s, b->ev_h2d[slot], 0);
+        k_batch_from_f64<<<xblocks((long long)n_in), 256, 0, s>>>(b->d_mem, count, b->d_in[slot],
+                                                                  (long long)n_in);
+        cudaEventRecord(b->ev_used[slot], s);
+    }
+    batch_fence(b, s, false);
+    rc = opo_batch_run(b, m);
+    if (rc != OPO_OK)
+        return rc;
+    if (host_out) {
+        batch_fence(b, s, true);
+        // the run may have moved the traces (they grow with m)
+        rc = batch_members(b, s);
+        if (rc != OPO_OK)
+            return rc;
+        // the slot's previous output has left for the host two steps ago
+        cudaStreamWaitEvent(s, b->ev_d2h[slot], 0);
+        k_batch_to_f64<<<xblocks((long long)n_out), 256, 0, s>>>(
+            b->d_mem, count, field, OPO_OUTPUT, b->d_out[slot], (long long)n_out);
+        // the last trace row of every member (the trace holds this call's m rows)
+        k_batch_last_row<<<xblocks(4LL * count), 256, 0, s>>>(b->d_mem, count, (int)m,
+                                                              b->d_out[slot] + 2 * n_out);
+        cudaEventRecord(b->ev_gath[slot], s);
+        batch_fence(b, s, false);
+        cudaStreamWaitEvent(b->io_out, b->ev_gath[slot], 0);
+        if (cudaMemcpyAsync(host_out, b->d_out[slot], sizeof(double) * out_doubles,
+                            cudaMemcpyDeviceToHost, b->io_out) != cudaSuccess)
+            return OPO_E_CUDA;
+        cudaEventRecord(b->ev_d2h[slot], b->io_out);
+    }
+    if (cudaGetLastError() != cudaSuccess)
+        return OPO_E_CUDA;
+    b->io_slot = slot ^ 1;
+    return OPO_OK;
+}
+
+int opo_batch_io_wait(opo_batch *b)
+{
+    if (!b)
+        return OPO_E_INVALID;
+    DeviceGuard g(b->device);
+    if (!g.ok)
+        return OPO_E_CUDA;
+    for (cudaStream_t st : {b->io_in, b->io_out})
+        if (st && cudaStreamSynchronize(st) != cudaSuccess)
+            return OPO_E_CUDA;
+    return batch_check_err(b);
 }
 
 int opo_batch_set_one_launch(opo_batch *b, int32_t on)

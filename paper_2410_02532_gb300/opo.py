@@ -102,6 +102,8 @@ _SIGS = {
     "opo_batch_get_fields": ([_P, ctypes.c_int32, ctypes.c_int32, _DP, ctypes.c_size_t],
                              ctypes.c_int),
     "opo_batch_get_trace": ([_P, _DP, ctypes.c_int64], ctypes.c_int),
+    "opo_batch_step_io": ([_P, _DP, _DP, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
+    "opo_batch_io_wait": ([_P], ctypes.c_int),
 }
 
 
@@ -280,6 +282,19 @@ def opo_batch_get_trace(batch, count, rows):
     _check(lib().opo_batch_get_trace(batch, out.ctypes.data_as(_DP), int(rows)),
            "opo_batch_get_trace")
     return out
+
+
+def opo_batch_step_io(batch, host_in, host_out, field, m=1):
+    """One batch step with overlapped host transfers (returns at once).
+    host_in / host_out: raw addresses (int) of page-locked double buffers, or
+    None; they must stay untouched until opo_batch_io_wait returns."""
+    _check(lib().opo_batch_step_io(batch, ctypes.cast(host_in, _DP) if host_in else None,
+                                   ctypes.cast(host_out, _DP) if host_out else None,
+                                   int(field), int(m)), "opo_batch_step_io")
+
+
+def opo_batch_io_wait(batch):
+    _check(lib().opo_batch_io_wait(batch), "opo_batch_io_wait")
 
 
 # ---- structs from a workload configuration ---------------------------------

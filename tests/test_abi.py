@@ -72,6 +72,8 @@ def test_null_arguments(L):
     assert L.opo_batch_set_fields(None, None, 0) == opo.OPO_E_INVALID
     assert L.opo_batch_get_fields(None, 0, 0, None, 0) == opo.OPO_E_INVALID
     assert L.opo_batch_get_trace(None, None, 0) == opo.OPO_E_INVALID
+    assert L.opo_batch_step_io(None, None, None, 0, 1) == opo.OPO_E_INVALID
+    assert L.opo_batch_io_wait(None) == opo.OPO_E_INVALID
     assert L.opo_set_output_history(None, 1) == opo.OPO_E_INVALID
     assert L.opo_get_output_history(None, 0, 0, 1, None) == opo.OPO_E_INVALID
 
