@@ -1125,21 +1125,35 @@ OPO_F2_DISPATCH_NL_DECL(dispatch_f32_f3_nodk);
 OPO_F2_DISPATCH_NL_DECL(dispatch_f32_f2_nodk);
 
 // Launch (op 0) or occupancy query (op 1) of one instantiation.
+// The cluster size compiled into an instantiation's batch shape, or 0 (a
+// runtime value): three FP32 fields, chi(2), in place: 8-CTA clusters at
+// 2^14, 16-CTA clusters at 2^16.  Exchange indices and cluster arithmetic
+// then become constants, with bit-identical results: 1.837 against 1.910 ms
+// per round trip of 36 instances at 2^14, 1.478 against 1.560 ms for 7
+// sync-pumped instances at 2^16.  (The FP64 2^14 kernel, bound by the FP64
+// pipe, gained nothing: 30.87 against 30.85 ms.)
+template <class T, int F, int LP, int LQ, bool IP, int NL, bool XG>
+constexpr int f2_compiled_cluster()
+{
+    if (!IP || XG || F != 3 || NL == kNlKerr || sizeof(T) != 4)
+        return 0;
+    if (LP == 7 && LQ == 7)
+        return 8;
+    if (LP == 8 && LQ == 8)
+        return 16;
+    return 0;
+}
+
 template <class T, int F, int LP, int LQ, bool IP, int NL, bool XG>
 int one_t(int op, const InstDesc *dd, int count, int C, int threads, size_t sm, bool ds,
           int r_base, int chunk, int last, cudaStream_t s)
 {
-    // the batch shape of the 2^14-point three-field FP32 chi(2) kernels
-    // (8-CTA clusters) has the cluster size compiled in: the exchange
-    // indices and cluster arithmetic become constants (1.837 against
-    // 1.910 ms per round trip of 36 instances, bit-identical results)
-    constexpr bool hot = sizeof(T) == 4 && F == 3 && LP == 7 && LQ == 7 && IP && !XG &&
-                         NL != kNlKerr;
-    if constexpr (hot) {
-        if (C == 8)
-            return op == 0 ? launch_t<T, F, LP, LQ, IP, NL, XG, 8>(dd, count, C, threads, sm, ds,
-                                                                   r_base, chunk, last, s)
-                           : max_active_t<T, F, LP, LQ, IP, NL, XG, 8>(C, threads, sm);
+    constexpr int CC = f2_compiled_cluster<T, F, LP, LQ, IP, NL, XG>();
+    if constexpr (CC > 0) {
+        if (C == CC)
+            return op == 0 ? launch_t<T, F, LP, LQ, IP, NL, XG, CC>(dd, count, C, threads, sm, ds,
+                                                                    r_base, chunk, last, s)
+                           : max_active_t<T, F, LP, LQ, IP, NL, XG, CC>(C, threads, sm);
     }
     return op == 0 ? launch_t<T, F, LP, LQ, IP, NL, XG>(dd, count, C, threads, sm, ds, r_base,
                                                         chunk, last, s)
