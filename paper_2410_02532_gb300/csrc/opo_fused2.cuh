@@ -101,6 +101,9 @@ __device__ __forceinline__ void rounds_loop(int items, const Ld &ld, const Work 
     }
 }
 
+#ifndef OPO_F2_ROT_REFRESH
+#define OPO_F2_ROT_REFRESH 0
+#endif
 template <class T, bool IP>
 constexpr int kF2MaxThreads = IP ? F2IpTraits<T>::kMaxThreads : F2Traits<T>::kMaxThreads;
 // Column split [Ra1, Ra2] = [2^A1, 2^A2] of a P = 2^LP column transform:
@@ -661,6 +664,10 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
 #pragma unroll
                 for (int r = 0; r < Ra2; r++) {
                     const int k1 = j + r * Ra1;
+#if OPO_F2_ROT_REFRESH
+                    if (r > 0 && r % OPO_F2_ROT_REFRESH == 0)
+                        w = twN((unsigned)(n2 * k1));
+#endif
                     rY[k1 >> logPc][RI(f, k1 & (Pc - 1), n2)] = cmul(v[r], w);
                     w = cmul(w, step);
                 }
@@ -906,6 +913,12 @@ __global__ void __launch_bounds__(kF2MaxThreadsL<T, F, IP, LP, NL>, 1)
 #pragma unroll
                 for (int r = 0; r < Rb1; r++) {
                     const int n2 = j + r * Rb2;
+#if OPO_F2_ROT_REFRESH
+                    if (r > 0 && r % OPO_F2_ROT_REFRESH == 0) {
+                        w = twN((unsigned)(k1 * n2));
+                        w.y = -w.y;
+                    }
+#endif
                     rX[n2 >> logQc][CI(f, k1, n2 & (Qc - 1))] = cmul(v[r], w);
                     w = cmul(w, step);
                 }
