@@ -166,7 +166,7 @@ def test_n16384_from_noise_through_saturation(prec, path):
 # held to the 1e-3 bar on both powers with the transient gone.  The signal
 # centroid has not settled: it is on a slow excursion (up to 11.2 THz at
 # ~11000 round trips, back to 9.7 THz at 20000, still moving ~4% per 2000
-# round trips), and FP32 rounding shifts the excursion's phase (15-20% apart
+# round trips), and FP32 rounding shifts the excursion's phase (8-20% apart
 # at 20000 round trips), so the centroid is recorded here, not held to a
 # steady-state bar; the FP64 path tracks the oracle's centroid within 1e-10
 # through the first 3000 round trips (above).
