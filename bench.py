@@ -36,8 +36,8 @@ METRIC = "SSFM field-steps/s at N=2^14 (fused, batched round trips)"
 # (instances, cluster, threads requested) -> DRAM bytes per fused launch of the
 # 2^14 workload (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture of the current kernel in that launch shape): 8-CTA clusters of 128
-# threads (cluster size compiled in), 48.08 MB read + 0.67 MB written
-PROFILED_SHAPES = {(36, 8, 128): 48748288.0}
+# threads (cluster size compiled in), 48.13 MB read + 0.80 MB written
+PROFILED_SHAPES = {(36, 8, 128): 48932608.0}
 UNIT = "field-steps/s"
 PEAK_SM_MHZ = 2070.0          # GB300 maximum SM clock
 SMS = 152
